@@ -1,0 +1,600 @@
+"""Benchmark of the GEMV / DOT / GER hot path on GB300.
+
+One step = one pass of the plain-method sweep through the C ABI, inputs
+uniform[-1,1] from the counter-based generator, resident in HBM:
+
+    for FP32 and FP64:
+      GEMV c += A x, A 16384x16384, 1048576x64 and 64x1048576, row-major
+      DOT  alpha += x.y, n = 2^28
+      GER  C += x y^T, 16384x16384, row-major
+      GEMV (the same three shapes), column-major
+      GER  16384x16384, column-major
+
+(18 kernel launches).  Every large operand (A, C, the DOT vectors) is bigger
+than the 129 MB L2 and consecutive calls touch different buffers, so no
+call starts with its operand in L2.  The metric is algorithmic HBM bytes
+(every element of A / C / x / y / c touched once) per second over the whole
+step; per-operation figures and the roofline of the dominant kernel are
+reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own replica on its own GPU (the operations
+do not shard: "replicas only"); the step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GEMV/DOT/GER HBM GB/s vs peak; served solves/s + p99 at stated error"
+WORKLOAD = ("plain-method sweep, FP32 and FP64: GEMV 16384x16384, 1048576x64, 64x1048576 "
+            "(row- and column-major), DOT n=2^28, GER 16384x16384 (row- and column-major); "
+            "inputs uniform[-1,1]")
+SQ, TALL, WIDE = (16384, 16384), (1048576, 64), (64, 1048576)
+NDOT = 1 << 28
+HBM_FALLBACK_GBS = 6800.0
+CPU_FRACTION = 16    # cpu_baseline sample: 1/16 of a step
+REF_FRACTION = 32    # reference arm: 1/32 of a step per step
+SMS, DP_FMA_PER_CLK_SM, SM_MAX_MHZ = 152, 2, 2070.0   # FP64 pipe: 2 FMA/clk/SM (1.26 TFLOP/s at 2.07 GHz)
+
+
+# --------------------------------------------------------------- workload --
+
+def op_list():
+    """(name, kind, dtype, layout, m, n) in launch order; dtype 'f32'/'f64'."""
+    ops = []
+    for dt in ("f32", "f64"):
+        for lay, tag in ((0, "row"), (1, "col")):
+            for (m, n), sh in ((SQ, "sq"), (TALL, "tall"), (WIDE, "wide")):
+                ops.append((f"gemv_{tag}_{sh}_{dt}", "gemv", dt, lay, m, n))
+            if lay == 0:
+                ops.append((f"dot_{dt}", "dot", dt, 0, 1, NDOT))
+            ops.append((f"ger_{tag}_{dt}", "ger", dt, lay, SQ[0], SQ[1]))
+    return ops
+
+
+def esize(dt):
+    return 4 if dt == "f32" else 8
+
+
+def alg_bytes(kind, dt, m, n):
+    """Compulsory HBM bytes of one call: every element touched once."""
+    e = esize(dt)
+    if kind == "gemv":
+        return e * (m * n + n + 2 * m)          # A, x read; c read and written
+    if kind == "dot":
+        return e * (2 * n + 2)                  # x, y read; alpha read and written
+    return e * (2 * m * n + m + n)              # C read and written; x, y read
+
+
+def alg_flops(kind, m, n):
+    return 2 * m * n if kind in ("gemv", "ger") else 2 * n
+
+
+class Workload:
+    """Device buffers of one step and a launcher for every operation."""
+
+    def __init__(self, device):
+        import torch
+        import synth
+        import paper_2108_02025_gb300 as gb
+        self.gb = gb
+        self.lib = gb.lib()
+        self.dev = device
+        self.ops = op_list()
+        self.buf = {}
+        tdt = {"f32": torch.float32, "f64": torch.float64}
+
+        def make(key, numel, dt, stream):
+            t = torch.empty(numel, dtype=tdt[dt], device=device)
+            synth.fill_uniform(t, 0, stream)
+            self.buf[key] = t
+            return t
+
+        st = gen_streams()
+        for dt in ("f32", "f64"):
+            for (m, n), sh in ((SQ, "sq"), (TALL, "tall"), (WIDE, "wide")):
+                make(("A", sh, dt), m * n, dt, st[("A", sh, dt)])
+                make(("x", sh, dt), n, dt, st[("x", sh, dt)])
+                make(("c", sh, dt), m, dt, st[("c", sh, dt)])
+            make(("dx", dt), NDOT, dt, st[("dx", dt)])
+            make(("dy", dt), NDOT, dt, st[("dy", dt)])
+            make(("alpha", dt), 1, dt, st[("alpha", dt)])
+            for tag in ("row", "col"):
+                make(("C", tag, dt), SQ[0] * SQ[1], dt, st[("C", tag, dt)])
+            make(("gx", dt), SQ[0], dt, st[("gx", dt)])
+            make(("gy", dt), SQ[1], dt, st[("gy", dt)])
+        # one zeroed workspace per operation (each call leaves it zeroed)
+        self.ws = {}
+        for (name, kind, dt, lay, m, n) in self.ops:
+            code = gb.F32 if dt == "f32" else gb.F64
+            op = gb.OP_GEMV if kind == "gemv" else gb.OP_DOT if kind == "dot" else gb.OP_GER
+            nb = gb.gb_workspace_bytes(op, code, lay, m, n)
+            self.ws[name] = (torch.zeros(max(nb, 1), dtype=torch.uint8, device=device), nb)
+        torch.cuda.synchronize(device)
+
+    def shape_key(self, m, n):
+        return "sq" if (m, n) == SQ else "tall" if (m, n) == TALL else "wide"
+
+    def launch(self, op, stream_handle):
+        name, kind, dt, lay, m, n = op
+        lib, b = self.lib, self.buf
+        ws, nb = self.ws[name]
+        if kind == "gemv":
+            sh = self.shape_key(m, n)
+            f = lib.gb_sgemv if dt == "f32" else lib.gb_dgemv
+            lda = n if lay == 0 else m
+            st = f(lay, m, n, 1.0, b[("A", sh, dt)].data_ptr(), lda, b[("x", sh, dt)].data_ptr(),
+                   b[("c", sh, dt)].data_ptr(), ws.data_ptr(), nb, stream_handle)
+        elif kind == "dot":
+            f = lib.gb_sdot if dt == "f32" else lib.gb_ddot
+            st = f(n, b[("dx", dt)].data_ptr(), b[("dy", dt)].data_ptr(), b[("alpha", dt)].data_ptr(),
+                   ws.data_ptr(), nb, stream_handle)
+        else:
+            tag = "row" if lay == 0 else "col"
+            f = lib.gb_sger if dt == "f32" else lib.gb_dger
+            st = f(lay, m, n, 1.0, b[("gx", dt)].data_ptr(), b[("gy", dt)].data_ptr(),
+                   b[("C", tag, dt)].data_ptr(), n if lay == 0 else m, stream_handle)
+        if st != 0:
+            raise RuntimeError(f"{name}: status {st} ({self.gb.gb_status_string(st)})")
+
+    # tensors each step reads from the host (e2e) and the results it returns
+    def inputs(self):
+        return [t for k, t in self.buf.items()]
+
+    def results(self):
+        b = self.buf
+        out = []
+        for dt in ("f32", "f64"):
+            out += [b[("c", sh, dt)] for sh in ("sq", "tall", "wide")]
+            out += [b[("alpha", dt)], b[("C", "row", dt)], b[("C", "col", dt)]]
+        return out
+
+
+# ----------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples taken every 100 ms."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.samples = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.5)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self, t0, t1):
+        inside = [p for (t, p) in self.samples if t0 <= t <= t1]
+        window = "timed region"
+        if len(inside) < 3:
+            inside = [p for (_, p) in self.samples]
+            window = "warm-up and timed region"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(p[1]) for p in inside if num(p[1]) is not None]
+        smax = [num(p[2]) for p in inside if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in inside for i in range(4) if p[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(inside), "window": window}
+
+
+# -------------------------------------------------------------- multi-GPU --
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return world, rank, local
+
+
+def init_dist(backend):
+    import torch.distributed as dist
+    world, rank, _ = dist_info()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend, world_size=world, rank=rank)
+    return world, rank
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Largest value over all ranks (the value itself without a group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(bytes_per_step: float, steps: int, world: int, max_seconds: float) -> float:
+    """GB/s of all replicas together: every rank moved bytes_per_step each step."""
+    return bytes_per_step * steps * world / max_seconds / 1e9
+
+
+# ------------------------------------------------------------ CPU oracle --
+
+def gen_streams():
+    """Generator stream of every buffer, in the order Workload fills them."""
+    st, s = {}, 1
+    for dt in ("f32", "f64"):
+        for sh in ("sq", "tall", "wide"):
+            st[("A", sh, dt)], st[("x", sh, dt)], st[("c", sh, dt)] = s, s + 1, s + 2
+            s += 3
+        st[("dx", dt)], st[("dy", dt)], st[("alpha", dt)] = s, s + 1, s + 2
+        s += 3
+        st[("C", "row", dt)], st[("C", "col", dt)] = s, s + 1
+        s += 2
+        st[("gx", dt)], st[("gy", dt)] = s, s + 1
+        s += 2
+    return st
+
+
+def oracle_sample(fraction: int, seed: int = 0):
+    """A bounded sample of one step for the CPU oracle: 1/fraction of the
+    rows of each row-major GEMV/GER (at least one), of the columns of each
+    column-major one, and of the DOT vectors, with the same generator values
+    the GPU step uses.  Returns [(callable, algorithmic bytes)]."""
+    import numpy as np
+    import oracle
+    import synth
+    st = gen_streams()
+    work = []
+    for (name, kind, dt, lay, m, n) in op_list():
+        npdt = np.float32 if dt == "f32" else np.float64
+        if kind == "gemv":
+            sh = "sq" if (m, n) == SQ else "tall" if (m, n) == TALL else "wide"
+            if lay == 0:
+                k = max(1, m // fraction)
+                A = synth.uniform(k * n, seed, st[("A", sh, dt)], npdt)
+                x = synth.uniform(n, seed, st[("x", sh, dt)], npdt)
+                c = synth.uniform(k, seed, st[("c", sh, dt)], npdt)
+                work.append((lambda A=A, x=x, c=c, k=k, n=n: oracle.gemv(0, k, n, 1.0, A, n, x, c, acc=False),
+                             alg_bytes("gemv", dt, k, n)))
+            else:
+                k = max(1, n // fraction)
+                A = synth.uniform(m * k, seed, st[("A", sh, dt)], npdt)
+                x = synth.uniform(k, seed, st[("x", sh, dt)], npdt)
+                c = synth.uniform(m, seed, st[("c", sh, dt)], npdt)
+                work.append((lambda A=A, x=x, c=c, k=k, m=m: oracle.gemv(1, m, k, 1.0, A, m, x, c, acc=False),
+                             alg_bytes("gemv", dt, m, k)))
+        elif kind == "dot":
+            k = max(1, n // fraction)
+            x = synth.uniform(k, seed, st[("dx", dt)], npdt)
+            y = synth.uniform(k, seed, st[("dy", dt)], npdt)
+            work.append((lambda x=x, y=y, k=k: oracle.dot(k, x, y, 0.0, acc=False),
+                         alg_bytes("dot", dt, 1, k)))
+        else:
+            tag = "row" if lay == 0 else "col"
+            k = max(1, (m if lay == 0 else n) // fraction)
+            C = synth.uniform(k * (n if lay == 0 else m), seed, st[("C", tag, dt)], npdt)
+            x = synth.uniform(m, seed, st[("gx", dt)], npdt)
+            y = synth.uniform(n, seed, st[("gy", dt)], npdt)
+            if lay == 0:
+                work.append((lambda C=C, x=x, y=y, k=k: oracle.ger(0, k, n, 1.0, x[:k], y, C, n),
+                             alg_bytes("ger", dt, k, n)))
+            else:
+                work.append((lambda C=C, x=x, y=y, k=k: oracle.ger(1, m, k, 1.0, x, y[:k], C, m),
+                             alg_bytes("ger", dt, m, k)))
+    return work
+
+
+def time_sample(work):
+    """Seconds the oracle takes over one pass of the sample, and its bytes."""
+    t, b = 0.0, 0
+    for f, by in work:
+        t0 = time.perf_counter()
+        f()
+        t += time.perf_counter() - t0
+        b += by
+    return t, b
+
+
+# -------------------------------------------------------------- roofline --
+
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2108_02025_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(op_name):
+    """DRAM bytes per launch of `op_name` from the committed ncu summary, or
+    None when absent or taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_sha") != source_sha():
+        return None
+    k = d.get("kernels", {}).get(op_name)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def roofline_of(op, avg_s, hbm_gbs, src):
+    name, kind, dt, lay, m, n = op
+    by = alg_bytes(kind, dt, m, n)
+    t_hbm = by / (hbm_gbs * 1e9)
+    dp_peak_tflops = SMS * DP_FMA_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    t_alu = alg_flops(kind, m, n) / (dp_peak_tflops * 1e12) if dt == "f64" else 0.0
+    if t_alu > t_hbm:
+        ach = alg_flops(kind, m, n) / avg_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": round(ach, 4),
+                "peak": round(dp_peak_tflops, 4), "unit": "TFLOP/s", "frac": round(ach / dp_peak_tflops, 4),
+                "traffic": measured_traffic(name),
+                "note": "FP64 FMA pipe, 152 SMs x 2 FMA/clk x 2.07 GHz; HBM frac "
+                        f"{by / avg_s / 1e9 / hbm_gbs:.3f} of {src}"}
+    ach = by / avg_s / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_gbs,
+            "unit": "GB/s", "frac": round(ach / hbm_gbs, 4), "peak_source": src,
+            "traffic": measured_traffic(name), "algorithmic_bytes": by}
+
+
+# ------------------------------------------------------------------- arms --
+
+def run_ours(args):
+    import torch
+    world, rank = init_dist("nccl")
+    _, _, local = dist_info()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    wl = Workload(device)
+    stream = torch.cuda.current_stream(device)
+    sh = stream.cuda_stream
+    ops = wl.ops
+
+    def step(evs=None):
+        for i, op in enumerate(ops):
+            if evs is not None:
+                evs[i][0].record(stream)
+            wl.launch(op, sh)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(device)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(2):  # keep the GPU busy while the sampler comes up
+        step()
+    per_op = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+               for _ in ops] for _ in range(args.steps)]
+    t_begin = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(device)
+    barrier()
+    wall0 = time.time()
+    t_begin.record(stream)
+    for k in range(args.steps):
+        step(per_op[k])
+    t_end.record(stream)
+    torch.cuda.synchronize(device)
+    barrier()
+    wall1 = time.time()
+    clocks.stop()
+    elapsed = t_begin.elapsed_time(t_end) / 1e3
+    elapsed_max = max_over_ranks(elapsed, device)
+
+    bytes_step = sum(alg_bytes(k, dt, m, n) for (_, k, dt, _, m, n) in ops)
+    value = whole_job_value(bytes_step, args.steps, world, elapsed_max)
+    op_times = [sum(per_op[k][i][0].elapsed_time(per_op[k][i][1]) for k in range(args.steps))
+                / args.steps / 1e3 for i in range(len(ops))]
+    hbm, src = peaks()
+    dom = max(range(len(ops)), key=lambda i: op_times[i])
+    ops_report = []
+    for i, (name, kind, dt, lay, m, n) in enumerate(ops):
+        gbs = alg_bytes(kind, dt, m, n) / op_times[i] / 1e9
+        ops_report.append({"op": name, "us": round(op_times[i] * 1e6, 2), "GB_s": round(gbs, 1),
+                           "frac_hbm": round(gbs / hbm, 4)})
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(wl, stream, device, bytes_step, args, world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        work = oracle_sample(CPU_FRACTION)
+        secs, sb = 0.0, 0
+        while secs < 10.0:          # repeat the sample until ~10 s of oracle time
+            t, b = time_sample(work)
+            secs, sb = secs + t, sb + b
+        cpu = {"value": round(sb / secs / 1e9, 3), "unit": "GB/s", "cores": oracle.threads(),
+               "kind": "oracle",
+               "sample": f"1/{CPU_FRACTION} of the rows (row-major) or columns (column-major) of "
+                         f"every GEMV/GER and of the DOT vectors of one step (DOT single-threaded), "
+                         f"plain FP64 oracle, repeated: {sb / 1e9:.2f} GB in {secs:.1f} s; "
+                         f"{os.cpu_count()} host cores"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(elapsed_max / args.steps * 1e3, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (each large operand >= 268 MB, L2 129 MB)",
+                       "bytes_per_step": bytes_step},
+            "roofline": roofline_of(ops[dom], op_times[dom], hbm, src),
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": len(ops) * args.steps,
+            "clocks": clocks.summary(wall0, wall1),
+            "ops": ops_report,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(wl, stream, device, bytes_step, args, world):
+    """The same step through host buffers: every step copies its inputs from
+    pinned host memory to the device, runs the 18 calls and copies the
+    results back."""
+    import torch
+    host_in = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in wl.inputs()]
+    for h, d in zip(host_in, wl.inputs()):
+        h.copy_(d)
+    res = wl.results()
+    host_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in res]
+    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    d2h = sum(t.numel() * t.element_size() for t in host_out)
+    sh = stream.cuda_stream
+    steps = max(1, min(args.steps, args.e2e_steps))
+
+    def step():
+        for h, d in zip(host_in, wl.inputs()):
+            d.copy_(h, non_blocking=True)
+        for op in wl.ops:
+            wl.launch(op, sh)
+        for h, d in zip(host_out, res):
+            h.copy_(d, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize(device)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    barrier()
+    secs = max_over_ranks(e0.elapsed_time(e1) / 1e3, device)
+    return {"value": round(whole_job_value(bytes_step, steps, world, secs), 1), "unit": "GB/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
+            "ms_per_step": round(secs / steps * 1e3, 3)}
+
+
+def run_reference(args):
+    """The oracle (plain FP64 CPU definitions) on the host cores, timed on a
+    bounded sample (1/REF_FRACTION) of the same step, on rank 0 only."""
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    work = oracle_sample(REF_FRACTION)
+    for _ in range(args.warmup):
+        time_sample(work)
+    total_b, total_t = 0, 0.0
+    for _ in range(args.steps):
+        secs, sb = time_sample(work)
+        total_b += sb
+        total_t += secs
+    threads = oracle.threads()
+    value = total_b / total_t / 1e9
+    sample = (f"each step: 1/{REF_FRACTION} of the rows (row-major) or columns (column-major) of every "
+              f"GEMV/GER and of the DOT vectors of one GPU step (DOT single-threaded), plain FP64 oracle, "
+              f"{total_b / args.steps / 1e9:.3f} GB per step")
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "impl": "reference",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_t / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": "host cores"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--e2e-steps", type=int, default=5, help="steps of the host-buffer (e2e) leg")
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    args = p.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        p.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

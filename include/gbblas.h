@@ -1,0 +1,167 @@
+/*
+ * gbblas.h — C ABI of the GB300 (sm_103a) GEMV / DOT / GER library.
+ *
+ * The three operations are the problem definitions of Singh & Bassoy, "High
+ * Performance Level-1 and Level-2 BLAS" (arXiv 2108.02025), Sec. 3.1, with a
+ * scale alpha on GEMV and GER:
+ *
+ *   GEMV (Def. GEMV; Alg. 1 column-major, Alg. 2 row-major):
+ *       c_i <- c_i + alpha * sum_j A_ij x_j,   i < m, j < n
+ *   DOT  (Def. DOT; Algs. 3 and 4):
+ *       *alpha <- *alpha + sum_p x_p y_p,      p < n   (alpha is the in/out
+ *       accumulator of the definition, not a scale)
+ *   GER  (Def. GEM; Alg. 2):
+ *       C_ij <- fma(x_i, fl(alpha * y_j), C_ij) i < m, j < n
+ *
+ * Matrix element (i, j) is M[i*ld + j] for GB_ROW_MAJOR (ld >= max(1, n)) and
+ * M[i + j*ld] for GB_COL_MAJOR (ld >= max(1, m)).  Vectors are contiguous
+ * (unit stride).
+ *
+ * Memory and ownership.  Every pointer argument except the stream is a
+ * DEVICE pointer owned by the caller (for example memory from PyTorch).  The
+ * library never allocates, frees or synchronises: each call validates its
+ * arguments on the host, enqueues its kernel(s) on `stream` and returns.
+ * Results are ready when the stream reaches that point.  A NULL stream is
+ * the legacy default stream.
+ *
+ * Workspace.  GEMV and DOT may split a sum across thread blocks; the partial
+ * sums and the arrival counters that pick the block which finishes the sum
+ * live in a caller-owned workspace of gb_workspace_bytes() bytes (0 means
+ * none is needed and ws may be NULL).  The workspace must be 16-byte aligned
+ * and zero-filled before its first use (gb_workspace_init, or memory that is
+ * already zero); every call leaves its counters at zero again, so one
+ * workspace serves any number of calls in stream order.  Two calls that run
+ * at the same time (different streams) must not share a workspace.
+ *
+ * Determinism.  The split of every sum depends only on (op, dtype, layout,
+ * m, n) and partial sums are combined in a fixed order with no floating
+ * point atomics, so repeated calls give bit-identical results.
+ *
+ * Errors.  Every function returns GB_OK (0) or a negative status:
+ *   -k (1 <= k < 100)  argument number k (1-based) is invalid; nothing was
+ *                      enqueued.  This covers m or n < 0, a leading
+ *                      dimension that is too small, a NULL pointer for a
+ *                      non-empty operand, an unknown layout, an output that
+ *                      overlaps an input, and a misaligned workspace;
+ *   GB_ERR_WORKSPACE   ws_bytes < gb_workspace_bytes(...);
+ *   GB_ERR_CUDA        the kernel launch failed (cudaPeekAtLastError);
+ *   GB_ERR_INJECTED    a fault requested through the GB_FAULT_INJECT
+ *                      environment variable (see below); nothing enqueued.
+ * Quick returns (GB_OK, nothing read or written): m == 0 or n == 0 for GEMV
+ * and GER; alpha == 0 for GEMV and GER; n == 0 for DOT (alpha unchanged).
+ * Pointers of any alignment are accepted; misaligned operands take a scalar
+ * GPU path.  There is no CPU fallback.
+ *
+ * Rounding.  IEEE round-to-nearest everywhere, no flush to zero.  GER is one
+ * fma per element and therefore exact to the last bit.  GEMV and DOT
+ * reassociate the sum (any order is a valid reading of the definitions);
+ * FP64 sums accumulate in FP64, FP32 GEMV accumulates in FP32 for at most 64
+ * terms at a time before moving the partial into FP64, FP32 DOT uses a
+ * compensated FP32 dot product per thread and FP64 above that, and the last
+ * reduction of DOT is always FP64.
+ *
+ * Fault injection (host side, for failure tests): GB_FAULT_INJECT=<op>:<k>
+ * with <op> one of gemv, dot, ger makes the k-th call (1-based, counted per
+ * op within the process, after argument validation) return GB_ERR_INJECTED
+ * without enqueuing anything.
+ */
+#ifndef GBBLAS_H
+#define GBBLAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { GB_ROW_MAJOR = 0, GB_COL_MAJOR = 1 } gb_layout;
+typedef enum { GB_OP_GEMV = 0, GB_OP_DOT = 1, GB_OP_GER = 2 } gb_op;
+typedef enum { GB_F32 = 0, GB_F64 = 1 } gb_dtype;
+
+enum {
+  GB_OK = 0,
+  GB_ERR_WORKSPACE = -100,
+  GB_ERR_UNSUPPORTED = -101,
+  GB_ERR_CUDA = -102,
+  GB_ERR_INJECTED = -103
+};
+
+/* A cudaStream_t passed as an opaque handle (NULL = legacy default stream). */
+typedef void *gb_stream;
+
+/* Library version, major*10000 + minor*100 + patch. */
+int gb_version(void);
+
+/* Text of a status code (static storage; never NULL). */
+const char *gb_status_string(int status);
+
+/* Bytes of workspace a call with these arguments needs (0 = none).  op is a
+   gb_op, dtype a gb_dtype, layout a gb_layout (ignored for DOT; m ignored
+   for DOT, where n is the vector length).  A pure function of its
+   arguments: it touches no device.  Invalid arguments give 0. */
+size_t gb_workspace_bytes(int op, int dtype, int layout, int64_t m, int64_t n);
+
+/* Zero ws_bytes bytes at ws on `stream` (cudaMemsetAsync).  Call once on a
+   fresh workspace.  Returns GB_OK, -1 if ws is NULL with ws_bytes > 0, or
+   GB_ERR_CUDA. */
+int gb_workspace_init(void *ws, size_t ws_bytes, gb_stream stream);
+
+/* GEMV, Def. GEMV (Sec. 3.1), Alg. 1 (column-major) and Alg. 2 (row-major):
+   c_i <- c_i + alpha * sum_j A_ij x_j for i < m.
+     layout  GB_ROW_MAJOR or GB_COL_MAJOR                         (arg 1)
+     m, n    rows and columns of A, >= 0                          (args 2, 3)
+     alpha   scale of the product                                 (arg 4)
+     A       device matrix, element (i, j) as described above     (arg 5)
+     lda     leading dimension (row-major >= max(1,n), col-major
+             >= max(1,m))                                         (arg 6)
+     x       device vector of n elements, read only               (arg 7)
+     c       device vector of m elements, read and written; must
+             not overlap A or x                                   (arg 8)
+     ws      device workspace (see above), 16-byte aligned        (arg 9)
+     ws_bytes its size in bytes                                   (arg 10)
+     stream  CUDA stream the kernels are enqueued on              (arg 11) */
+int gb_dgemv(int layout, int64_t m, int64_t n, double alpha, const double *A, int64_t lda,
+             const double *x, double *c, void *ws, size_t ws_bytes, gb_stream stream);
+int gb_sgemv(int layout, int64_t m, int64_t n, float alpha, const float *A, int64_t lda,
+             const float *x, float *c, void *ws, size_t ws_bytes, gb_stream stream);
+
+/* DOT, Def. DOT (Sec. 3.1), Alg. 3 (one block for small n) and Alg. 4
+   (blocks of the index range, then one combined sum for large n):
+   *alpha <- *alpha + sum_p x_p y_p.
+     n       vector length, >= 0                                  (arg 1)
+     x, y    device vectors of n elements, read only              (args 2, 3)
+     alpha   device pointer to ONE element, read and written;
+             must not overlap x or y                              (arg 4)
+     ws, ws_bytes, stream as for GEMV                             (args 5-7)
+   The sum of products is formed in FP64 (FP32 inputs: compensated FP32
+   per thread, FP64 above), added to *alpha in FP64 and rounded once to the
+   element type. */
+int gb_ddot(int64_t n, const double *x, const double *y, double *alpha, void *ws,
+            size_t ws_bytes, gb_stream stream);
+int gb_sdot(int64_t n, const float *x, const float *y, float *alpha, void *ws, size_t ws_bytes,
+            gb_stream stream);
+
+/* GER, Def. GEM (Sec. 3.1), Alg. 2: C_ij <- fma(x_i, t_j, C_ij) with
+   t_j = fl(alpha * y_j), one rounding per element (bit-exact).  Every
+   element of C has exactly one writer.
+     layout  GB_ROW_MAJOR or GB_COL_MAJOR                         (arg 1)
+     m, n    rows and columns of C, >= 0                          (args 2, 3)
+     alpha   scale                                                (arg 4)
+     x       device vector of m elements                          (arg 5)
+     y       device vector of n elements                          (arg 6)
+     C       device matrix, read and written; must not overlap
+             x or y                                               (arg 7)
+     ldc     leading dimension of C                               (arg 8)
+     stream  CUDA stream                                          (arg 9)
+   Needs no workspace. */
+int gb_dger(int layout, int64_t m, int64_t n, double alpha, const double *x, const double *y,
+            double *C, int64_t ldc, gb_stream stream);
+int gb_sger(int layout, int64_t m, int64_t n, float alpha, const float *x, const float *y,
+            float *C, int64_t ldc, gb_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBBLAS_H */

@@ -1,0 +1,217 @@
+"""Python binding of libgbblas.so — GEMV, DOT and GER on one GB300 (sm_103a).
+
+The functions ``gb_*`` have the names and argument order of the C ABI in
+``include/gbblas.h`` and only marshal arguments: tensors become device
+pointers, a ``torch.cuda.Stream`` becomes its handle, and the C status code
+is returned unchanged.  ``gemv``, ``dot`` and ``ger`` are convenience calls
+over them that pick the dtype variant, hold a zeroed workspace per device
+and stream, and raise ``GbError`` on a non-zero status.
+
+The library must be built (``__graft_entry__.build()`` or
+``python paper_2108_02025_gb300/build.py``); importing this package without
+it raises.  There is no CPU implementation: every operation runs in the
+library's kernels on the GPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+# GBBLAS_LIB overrides where the library is loaded from.
+LIB_PATH = os.environ.get("GBBLAS_LIB", os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                     "libgbblas.so"))
+
+ROW_MAJOR, COL_MAJOR = 0, 1
+OP_GEMV, OP_DOT, OP_GER = 0, 1, 2
+F32, F64 = 0, 1
+
+GB_OK = 0
+GB_ERR_WORKSPACE = -100
+GB_ERR_UNSUPPORTED = -101
+GB_ERR_CUDA = -102
+GB_ERR_INJECTED = -103
+
+
+class GbError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: status {status} ({gb_status_string(status)})")
+        self.status = status
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run __graft_entry__.build() "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    I, I64, P, SZ = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t
+    D, F = ctypes.c_double, ctypes.c_float
+    lib.gb_version.argtypes, lib.gb_version.restype = [], I
+    lib.gb_status_string.argtypes, lib.gb_status_string.restype = [I], ctypes.c_char_p
+    lib.gb_workspace_bytes.argtypes, lib.gb_workspace_bytes.restype = [I, I, I, I64, I64], SZ
+    lib.gb_workspace_init.argtypes, lib.gb_workspace_init.restype = [P, SZ, P], I
+    lib.gb_dgemv.argtypes = [I, I64, I64, D, P, I64, P, P, P, SZ, P]
+    lib.gb_sgemv.argtypes = [I, I64, I64, F, P, I64, P, P, P, SZ, P]
+    lib.gb_ddot.argtypes = [I64, P, P, P, P, SZ, P]
+    lib.gb_sdot.argtypes = [I64, P, P, P, P, SZ, P]
+    lib.gb_dger.argtypes = [I, I64, I64, D, P, P, P, I64, P]
+    lib.gb_sger.argtypes = [I, I64, I64, F, P, P, P, I64, P]
+    for name in ("gb_dgemv", "gb_sgemv", "gb_ddot", "gb_sdot", "gb_dger", "gb_sger"):
+        getattr(lib, name).restype = I
+    return lib
+
+
+_lib = _load()
+
+# Every symbol the header declares (checked by the tests against include/gbblas.h).
+EXPORTS = ("gb_version", "gb_status_string", "gb_workspace_bytes", "gb_workspace_init",
+           "gb_dgemv", "gb_sgemv", "gb_ddot", "gb_sdot", "gb_dger", "gb_sger")
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+# ------------------------------------------------------------ marshalling --
+
+def _ptr(t) -> int | None:
+    """Device pointer of a tensor, or an int passed through (None = NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ------------------------------------------------------------------ C ABI --
+
+def gb_version() -> int:
+    return _lib.gb_version()
+
+
+def gb_status_string(status: int) -> str:
+    return _lib.gb_status_string(status).decode()
+
+
+def gb_workspace_bytes(op: int, dtype: int, layout: int, m: int, n: int) -> int:
+    return _lib.gb_workspace_bytes(op, dtype, layout, m, n)
+
+
+def gb_workspace_init(ws, ws_bytes: int, stream=None) -> int:
+    return _lib.gb_workspace_init(_ptr(ws), ws_bytes, _stream(stream))
+
+
+def gb_dgemv(layout, m, n, alpha, A, lda, x, c, ws, ws_bytes, stream=None) -> int:
+    return _lib.gb_dgemv(layout, m, n, alpha, _ptr(A), lda, _ptr(x), _ptr(c), _ptr(ws), ws_bytes,
+                         _stream(stream))
+
+
+def gb_sgemv(layout, m, n, alpha, A, lda, x, c, ws, ws_bytes, stream=None) -> int:
+    return _lib.gb_sgemv(layout, m, n, alpha, _ptr(A), lda, _ptr(x), _ptr(c), _ptr(ws), ws_bytes,
+                         _stream(stream))
+
+
+def gb_ddot(n, x, y, alpha, ws, ws_bytes, stream=None) -> int:
+    return _lib.gb_ddot(n, _ptr(x), _ptr(y), _ptr(alpha), _ptr(ws), ws_bytes, _stream(stream))
+
+
+def gb_sdot(n, x, y, alpha, ws, ws_bytes, stream=None) -> int:
+    return _lib.gb_sdot(n, _ptr(x), _ptr(y), _ptr(alpha), _ptr(ws), ws_bytes, _stream(stream))
+
+
+def gb_dger(layout, m, n, alpha, x, y, C, ldc, stream=None) -> int:
+    return _lib.gb_dger(layout, m, n, alpha, _ptr(x), _ptr(y), _ptr(C), ldc, _stream(stream))
+
+
+def gb_sger(layout, m, n, alpha, x, y, C, ldc, stream=None) -> int:
+    return _lib.gb_sger(layout, m, n, alpha, _ptr(x), _ptr(y), _ptr(C), ldc, _stream(stream))
+
+
+# ---------------------------------------------------------- convenience ----
+
+_ws_lock = threading.Lock()
+_ws_cache: dict = {}
+
+
+def workspace(nbytes: int, device=None, stream=None):
+    """A zero-filled uint8 device buffer of at least ``nbytes`` for ``stream``,
+    kept and reused by later calls on the same (device, stream)."""
+    import torch
+    if nbytes <= 0:
+        return None
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else
+                       torch.device(device).index or 0)
+    key = (dev.index, _stream(stream))
+    with _ws_lock:
+        buf = _ws_cache.get(key)
+        if buf is None or buf.numel() < nbytes:
+            buf = torch.zeros(max(nbytes, 1 << 16), dtype=torch.uint8, device=dev)
+            _ws_cache[key] = buf
+    return buf
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _check(status: int, what: str) -> None:
+    if status != GB_OK:
+        raise GbError(status, what)
+
+
+def gemv(A, x, c, alpha: float = 1.0, layout: int = ROW_MAJOR, m: int | None = None,
+         n: int | None = None, lda: int | None = None, stream=None) -> None:
+    """c += alpha * A @ x in place.  ``A`` is a 2-D CUDA tensor in its own
+    memory order (row-major: stride (lda, 1); column-major: stride (1, lda)),
+    or a flat buffer with m, n, lda given."""
+    if A.dim() == 2 and m is None:
+        m, n = A.shape
+        if layout == ROW_MAJOR:
+            assert A.stride(1) == 1 or n <= 1, "row-major A needs unit column stride"
+            lda = A.stride(0) if m > 1 else max(1, n)
+        else:
+            assert A.stride(0) == 1 or m <= 1, "column-major A needs unit row stride"
+            lda = A.stride(1) if n > 1 else max(1, m)
+    dt = _dtype_code(A)
+    nb = gb_workspace_bytes(OP_GEMV, dt, layout, m, n)
+    ws = workspace(nb, A.device, stream)
+    f = gb_dgemv if dt == F64 else gb_sgemv
+    _check(f(layout, m, n, alpha, A, lda, x, c, ws, nb, stream), "gemv")
+
+
+def dot(x, y, alpha, n: int | None = None, stream=None) -> None:
+    """alpha += x . y in place; ``alpha`` is a one-element CUDA tensor."""
+    n = x.numel() if n is None else n
+    dt = _dtype_code(x)
+    nb = gb_workspace_bytes(OP_DOT, dt, 0, 0, n)
+    ws = workspace(nb, x.device, stream)
+    f = gb_ddot if dt == F64 else gb_sdot
+    _check(f(n, x, y, alpha, ws, nb, stream), "dot")
+
+
+def ger(x, y, C, alpha: float = 1.0, layout: int = ROW_MAJOR, m: int | None = None,
+        n: int | None = None, ldc: int | None = None, stream=None) -> None:
+    """C += alpha * outer(x, y) in place (one fma per element)."""
+    if C.dim() == 2 and m is None:
+        m, n = C.shape
+        if layout == ROW_MAJOR:
+            ldc = C.stride(0) if m > 1 else max(1, n)
+        else:
+            ldc = C.stride(1) if n > 1 else max(1, m)
+    dt = _dtype_code(C)
+    f = gb_dger if dt == F64 else gb_sger
+    _check(f(layout, m, n, alpha, x, y, C, ldc, stream), "ger")

@@ -1,0 +1,401 @@
+// C ABI of the library (declared in include/gbblas.h): argument checks,
+// work plans, workspace layout and kernel dispatch.  Host code only; nothing
+// here allocates, frees or synchronises.
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/gbblas.h"
+#include "gb_internal.h"
+
+namespace gb {
+namespace {
+
+constexpr int64_t kTargetUnits = 608;   // one wave of 4 blocks on each of 152 SMs
+constexpr int kMaxSplits = 512;
+constexpr int64_t kDotSmall = 16384;    // up to here DOT is one block (Alg. 3)
+constexpr int64_t kDotBlocks = 608;     // large DOT: at most this many blocks (Alg. 4)
+constexpr int kDotPack = 4;             // packs per thread per step in the DOT kernel
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t pow2_at_least(int64_t v, int64_t cap) {
+  int64_t p = 1;
+  while (p < v && p < cap) p <<= 1;
+  return p;
+}
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// [lo, hi) byte ranges overlap?
+inline bool overlap(const void* a, unsigned __int128 abytes, const void* b, unsigned __int128 bbytes) {
+  if (abytes == 0 || bbytes == 0) return false;
+  const unsigned __int128 a0 = reinterpret_cast<uintptr_t>(a), b0 = reinterpret_cast<uintptr_t>(b);
+  return a0 < b0 + bbytes && b0 < a0 + abytes;
+}
+
+// Bytes spanned by an m x n matrix with leading dimension ld.
+inline unsigned __int128 matrix_bytes(int layout, int64_t m, int64_t n, int64_t ld, size_t e) {
+  if (m == 0 || n == 0) return 0;
+  const unsigned __int128 lines = layout == GB_ROW_MAJOR ? m : n;
+  const unsigned __int128 len = layout == GB_ROW_MAJOR ? n : m;
+  return ((lines - 1) * (unsigned __int128)ld + len) * e;
+}
+
+// ---------------------------------------------------------------- plans ---
+
+struct SplitShape {
+  int S, NG;
+  int64_t kc, tiles;
+};
+
+inline size_t split_bytes(const SplitShape& s, int64_t m) {
+  if (s.S <= 1) return 0;
+  const size_t tick = (size_t)s.tiles * (s.NG + 1) * sizeof(unsigned);
+  const size_t tick_pad = (tick + 255) / 256 * 256;
+  return tick_pad + (size_t)s.S * m * sizeof(double) + (s.NG > 1 ? (size_t)s.NG * m * sizeof(double) : 0);
+}
+
+inline Split split_view(const SplitShape& s, int64_t m, void* ws) {
+  Split sp{s.S, s.NG, m, nullptr, nullptr, nullptr};
+  if (s.S <= 1) return sp;
+  const size_t tick = (size_t)s.tiles * (s.NG + 1) * sizeof(unsigned);
+  const size_t tick_pad = (tick + 255) / 256 * 256;
+  char* base = static_cast<char*>(ws);
+  sp.tickets = reinterpret_cast<unsigned*>(base);
+  sp.part = reinterpret_cast<double*>(base + tick_pad);
+  sp.part2 = s.NG > 1 ? sp.part + (size_t)s.S * m : nullptr;
+  return sp;
+}
+
+// Number of chunks for `tiles` row tiles over a summed index of length n
+// whose chunks must hold at least `min_kc` indices and be multiples of
+// `quantum`.  Depends only on the shape.
+inline SplitShape choose_split(int64_t tiles, int64_t n, int64_t min_kc, int64_t quantum) {
+  SplitShape s{1, 1, n > 0 ? n : 1, tiles};
+  if (tiles >= kTargetUnits / 2 || n <= min_kc) return s;
+  int64_t S = kTargetUnits / tiles;
+  if (S > kMaxSplits) S = kMaxSplits;
+  const int64_t smax = n / min_kc;
+  if (S > smax) S = smax;
+  if (S < 2) return s;
+  int64_t kc = cdiv(cdiv(n, S), quantum) * quantum;
+  S = cdiv(n, kc);
+  if (S < 2) return s;
+  s.S = (int)S;
+  s.NG = (int)cdiv(S, kGroup);
+  s.kc = kc;
+  return s;
+}
+
+struct RowShape {
+  int lpr, rw;
+  SplitShape sp;
+};
+
+inline RowShape row_shape(size_t e, bool vec, int64_t m, int64_t n) {
+  const int64_t V = vec ? 16 / (int64_t)e : 1;
+  RowShape r;
+  const int64_t packs = cdiv(n, V);
+  r.lpr = (int)pow2_at_least(packs, 32);
+  r.rw = packs <= 2 * 32 ? 8 : 4;
+  const int64_t rows = (256 / r.lpr) * r.rw;
+  r.sp = choose_split(cdiv(m, rows), n, r.lpr * V * 2 * 4, r.lpr * V);
+  return r;
+}
+
+struct ColShape {
+  int tx;
+  SplitShape sp;
+};
+
+inline ColShape col_shape(size_t e, bool vec, int64_t m, int64_t n) {
+  const int64_t V = vec ? 16 / (int64_t)e : 1;
+  ColShape c;
+  c.tx = (int)pow2_at_least(cdiv(m, V), 64);
+  const int64_t ty = 256 / c.tx;
+  c.sp = choose_split(cdiv(m, c.tx * V), n, ty * 4 * 4, 1);
+  return c;
+}
+
+inline void dot_shape(size_t e, bool vec, int64_t n, int64_t* chunk, int64_t* blocks) {
+  if (n <= kDotSmall) {
+    *chunk = n;
+    *blocks = 1;
+    return;
+  }
+  const int64_t V = vec ? 16 / (int64_t)e : 1;
+  const int64_t q = 256 * V * kDotPack;
+  int64_t G = cdiv(n, q);
+  if (G > kDotBlocks) G = kDotBlocks;
+  *chunk = cdiv(cdiv(n, G), q) * q;
+  *blocks = cdiv(n, *chunk);
+}
+
+inline size_t dot_bytes(int64_t blocks) {
+  return blocks <= 1 ? 0 : 256 + (size_t)blocks * sizeof(double);
+}
+
+// The workspace size does not depend on pointer alignment: both variants
+// are sized and the larger is reported.
+size_t gemv_ws(size_t e, int layout, int64_t m, int64_t n) {
+  size_t b = 0;
+  for (int vec = 0; vec < 2; ++vec) {
+    const SplitShape s = layout == GB_ROW_MAJOR ? row_shape(e, vec, m, n).sp : col_shape(e, vec, m, n).sp;
+    const size_t w = split_bytes(s, m);
+    if (w > b) b = w;
+  }
+  return b;
+}
+
+size_t dot_ws(size_t e, int64_t n) {
+  size_t b = 0;
+  for (int vec = 0; vec < 2; ++vec) {
+    int64_t chunk, blocks;
+    dot_shape(e, vec, n, &chunk, &blocks);
+    const size_t w = dot_bytes(blocks);
+    if (w > b) b = w;
+  }
+  return b;
+}
+
+// ------------------------------------------------------- fault injection ---
+
+struct Inject {
+  int op = -1;
+  long long nth = 0;
+  std::atomic<long long> count[3] = {0, 0, 0};
+};
+
+Inject& inject() {
+  static Inject inj;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const char* v = std::getenv("GB_FAULT_INJECT");
+    if (!v) return;
+    const char* colon = std::strchr(v, ':');
+    if (!colon) return;
+    const size_t len = (size_t)(colon - v);
+    if (len == 4 && std::strncmp(v, "gemv", 4) == 0) inj.op = GB_OP_GEMV;
+    else if (len == 3 && std::strncmp(v, "dot", 3) == 0) inj.op = GB_OP_DOT;
+    else if (len == 3 && std::strncmp(v, "ger", 3) == 0) inj.op = GB_OP_GER;
+    inj.nth = std::atoll(colon + 1);
+  });
+  return inj;
+}
+
+inline bool injected(int op) {
+  Inject& inj = inject();
+  const long long k = inj.count[op].fetch_add(1) + 1;
+  return inj.op == op && k == inj.nth;
+}
+
+inline int cuda_status() {
+  return cudaPeekAtLastError() == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+// ------------------------------------------------------------- dispatch ---
+
+template <typename T>
+int gemv(int layout, int64_t m, int64_t n, T alpha, const T* A, int64_t lda, const T* x, T* c,
+         void* ws, size_t ws_bytes, gb_stream stream) {
+  if (layout != GB_ROW_MAJOR && layout != GB_COL_MAJOR) return -1;
+  if (m < 0) return -2;
+  if (n < 0) return -3;
+  const int64_t min_ld = layout == GB_ROW_MAJOR ? (n > 1 ? n : 1) : (m > 1 ? m : 1);
+  if (lda < min_ld) return -6;
+  if (m == 0 || n == 0 || alpha == T(0)) return GB_OK;
+  if (!A) return -5;
+  if (!x) return -7;
+  if (!c) return -8;
+  const size_t e = sizeof(T);
+  const unsigned __int128 cb = (unsigned __int128)m * e;
+  if (overlap(c, cb, A, matrix_bytes(layout, m, n, lda, e)) || overlap(c, cb, x, (unsigned __int128)n * e))
+    return -8;
+  const size_t need = gemv_ws(e, layout, m, n);
+  if (need > 0 && (!ws || !aligned16(ws))) return -9;
+  if (ws_bytes < need) return GB_ERR_WORKSPACE;
+  if (injected(GB_OP_GEMV)) return GB_ERR_INJECTED;
+
+  const int64_t V = 16 / (int64_t)e;
+  const bool vec = aligned16(A) && aligned16(x) && lda % V == 0;
+  GemvArgs<T> a{m, n, alpha, A, lda, x, c};
+  GemvPlan p{};
+  p.vec = vec;
+  SplitShape s;
+  if (layout == GB_ROW_MAJOR) {
+    const RowShape r = row_shape(e, vec, m, n);
+    p.lpr = r.lpr;
+    p.rw = r.rw;
+    s = r.sp;
+  } else {
+    const ColShape cs = col_shape(e, vec, m, n);
+    p.tx = cs.tx;
+    s = cs.sp;
+  }
+  p.kc = s.kc;
+  p.tiles = s.tiles;
+  p.units = s.tiles * s.S;
+  p.split = split_view(s, m, ws);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (layout == GB_ROW_MAJOR) gemv_row_launch<T>(a, p, st);
+  else gemv_col_launch<T>(a, p, st);
+  return cuda_status();
+}
+
+template <typename T>
+int dot(int64_t n, const T* x, const T* y, T* alpha, void* ws, size_t ws_bytes, gb_stream stream) {
+  if (n < 0) return -1;
+  if (n == 0) return GB_OK;
+  if (!x) return -2;
+  if (!y) return -3;
+  if (!alpha) return -4;
+  const size_t e = sizeof(T);
+  if (overlap(alpha, e, x, (unsigned __int128)n * e) || overlap(alpha, e, y, (unsigned __int128)n * e))
+    return -4;
+  const size_t need = dot_ws(e, n);
+  if (need > 0 && (!ws || !aligned16(ws))) return -5;
+  if (ws_bytes < need) return GB_ERR_WORKSPACE;
+  if (injected(GB_OP_DOT)) return GB_ERR_INJECTED;
+
+  DotArgs<T> a{n, x, y, alpha};
+  DotPlan p{};
+  p.vec = aligned16(x) && aligned16(y);
+  dot_shape(e, p.vec, n, &p.chunk, &p.blocks);
+  if (p.blocks > 1) {
+    p.ticket = static_cast<unsigned*>(ws);
+    p.part = reinterpret_cast<double*>(static_cast<char*>(ws) + 256);
+  }
+  dot_launch<T>(a, p, static_cast<cudaStream_t>(stream));
+  return cuda_status();
+}
+
+template <typename T>
+int ger(int layout, int64_t m, int64_t n, T alpha, const T* x, const T* y, T* C, int64_t ldc,
+        gb_stream stream) {
+  if (layout != GB_ROW_MAJOR && layout != GB_COL_MAJOR) return -1;
+  if (m < 0) return -2;
+  if (n < 0) return -3;
+  const int64_t min_ld = layout == GB_ROW_MAJOR ? (n > 1 ? n : 1) : (m > 1 ? m : 1);
+  if (ldc < min_ld) return -8;
+  if (m == 0 || n == 0 || alpha == T(0)) return GB_OK;
+  if (!x) return -5;
+  if (!y) return -6;
+  if (!C) return -7;
+  const size_t e = sizeof(T);
+  const unsigned __int128 cb = matrix_bytes(layout, m, n, ldc, e);
+  if (overlap(C, cb, x, (unsigned __int128)m * e) || overlap(C, cb, y, (unsigned __int128)n * e)) return -7;
+  if (injected(GB_OP_GER)) return GB_ERR_INJECTED;
+
+  const int64_t V = 16 / (int64_t)e;
+  GerArgs<T> a{m, n, alpha, x, y, C, ldc};
+  GerPlan p{};
+  p.row = layout == GB_ROW_MAJOR;
+  p.lines = p.row ? m : n;
+  p.len = p.row ? n : m;
+  p.vec = aligned16(C) && ldc % V == 0 && aligned16(p.row ? (const void*)y : (const void*)x);
+  ger_launch<T>(a, p, static_cast<cudaStream_t>(stream));
+  return cuda_status();
+}
+
+}  // namespace
+
+// Occupancy of each kernel is queried once per (kernel, device).
+int grid_size(const void* kernel, int64_t units, size_t smem) {
+  struct Entry {
+    const void* k;
+    int dev;
+    int blocks;
+  };
+  static Entry cache[256];
+  static int used = 0;
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int blocks = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < used; ++i)
+      if (cache[i].k == kernel && cache[i].dev == dev) blocks = cache[i].blocks;
+    if (blocks == 0) {
+      int sms = 0, per_sm = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+      blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+      if (used < 256) cache[used++] = Entry{kernel, dev, blocks};
+    }
+  }
+  return (int)(units < blocks ? (units > 0 ? units : 1) : blocks);
+}
+
+}  // namespace gb
+
+// ------------------------------------------------------------------ C ABI ---
+
+extern "C" {
+
+int gb_version(void) { return 100; }
+
+const char* gb_status_string(int status) {
+  switch (status) {
+    case GB_OK: return "GB_OK: success";
+    case GB_ERR_WORKSPACE: return "GB_ERR_WORKSPACE: workspace smaller than gb_workspace_bytes()";
+    case GB_ERR_UNSUPPORTED: return "GB_ERR_UNSUPPORTED: unsupported argument combination";
+    case GB_ERR_CUDA: return "GB_ERR_CUDA: kernel launch failed";
+    case GB_ERR_INJECTED: return "GB_ERR_INJECTED: fault injected through GB_FAULT_INJECT";
+    default: break;
+  }
+  if (status < 0 && status > -100) return "invalid argument (status -k: argument k)";
+  return "unknown status";
+}
+
+size_t gb_workspace_bytes(int op, int dtype, int layout, int64_t m, int64_t n) {
+  if (dtype != GB_F32 && dtype != GB_F64) return 0;
+  const size_t e = dtype == GB_F32 ? 4 : 8;
+  if (op == GB_OP_DOT) return n > 0 ? gb::dot_ws(e, n) : 0;
+  if (op == GB_OP_GEMV) {
+    if (layout != GB_ROW_MAJOR && layout != GB_COL_MAJOR) return 0;
+    if (m <= 0 || n <= 0) return 0;
+    return gb::gemv_ws(e, layout, m, n);
+  }
+  return 0;
+}
+
+int gb_workspace_init(void* ws, size_t ws_bytes, gb_stream stream) {
+  if (ws_bytes == 0) return GB_OK;
+  if (!ws) return -1;
+  return cudaMemsetAsync(ws, 0, ws_bytes, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? GB_OK
+             : GB_ERR_CUDA;
+}
+
+int gb_dgemv(int layout, int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
+             const double* x, double* c, void* ws, size_t ws_bytes, gb_stream stream) {
+  return gb::gemv<double>(layout, m, n, alpha, A, lda, x, c, ws, ws_bytes, stream);
+}
+
+int gb_sgemv(int layout, int64_t m, int64_t n, float alpha, const float* A, int64_t lda,
+             const float* x, float* c, void* ws, size_t ws_bytes, gb_stream stream) {
+  return gb::gemv<float>(layout, m, n, alpha, A, lda, x, c, ws, ws_bytes, stream);
+}
+
+int gb_ddot(int64_t n, const double* x, const double* y, double* alpha, void* ws, size_t ws_bytes,
+            gb_stream stream) {
+  return gb::dot<double>(n, x, y, alpha, ws, ws_bytes, stream);
+}
+
+int gb_sdot(int64_t n, const float* x, const float* y, float* alpha, void* ws, size_t ws_bytes,
+            gb_stream stream) {
+  return gb::dot<float>(n, x, y, alpha, ws, ws_bytes, stream);
+}
+
+int gb_dger(int layout, int64_t m, int64_t n, double alpha, const double* x, const double* y,
+            double* C, int64_t ldc, gb_stream stream) {
+  return gb::ger<double>(layout, m, n, alpha, x, y, C, ldc, stream);
+}
+
+int gb_sger(int layout, int64_t m, int64_t n, float alpha, const float* x, const float* y,
+            float* C, int64_t ldc, gb_stream stream) {
+  return gb::ger<float>(layout, m, n, alpha, x, y, C, ldc, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+// Host-side plumbing shared by the kernel files and the C ABI (api.cu).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gb_split.h"
+
+namespace gb {
+
+constexpr int kThreads = 256;  // every kernel runs 256-thread blocks
+
+template <typename T>
+struct GemvArgs {
+  int64_t m, n;
+  T alpha;
+  const T* A;
+  int64_t lda;
+  const T* x;
+  T* c;
+};
+
+// How one GEMV is cut into work units.  Depends only on (dtype, layout, m, n)
+// and pointer alignment (which selects the 16-byte or the scalar variant;
+// both sum in the same per-lane order only for the same variant).
+struct GemvPlan {
+  bool vec;        // 16-byte packs (A, x 16-byte aligned and lda a multiple of the pack)
+  int lpr;         // row-major: lanes per row (1..32)
+  int rw;          // row-major: rows per lane group
+  int tx;          // column-major: threads along the rows of a tile
+  int64_t kc;      // columns per chunk
+  int64_t tiles;   // row tiles
+  int64_t units;   // tiles * S
+  Split split;     // S chunks of the summed index (S = 1: no split) and their workspace
+};
+
+template <typename T>
+struct DotArgs {
+  int64_t n;
+  const T* x;
+  const T* y;
+  T* alpha;
+};
+
+struct DotPlan {
+  bool vec;
+  int64_t chunk;   // elements per block
+  int64_t blocks;  // number of blocks (1 = the single-block form, Alg. 3)
+  double* part;
+  unsigned* ticket;
+};
+
+template <typename T>
+struct GerArgs {
+  int64_t m, n;
+  T alpha;
+  const T* x;
+  const T* y;
+  T* C;
+  int64_t ldc;
+};
+
+struct GerPlan {
+  bool vec;
+  bool row;        // row-major: lines are rows
+  int64_t lines, len;
+};
+
+// Blocks to launch for `units` independent work units: every SM filled to
+// the kernel's occupancy, never more blocks than units.
+int grid_size(const void* kernel, int64_t units, size_t smem = 0);
+
+template <typename T>
+int gemv_row_launch(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st);
+template <typename T>
+int gemv_col_launch(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st);
+template <typename T>
+int dot_launch(const DotArgs<T>& a, const DotPlan& p, cudaStream_t st);
+template <typename T>
+int ger_launch(const GerArgs<T>& a, const GerPlan& p, cudaStream_t st);
+
+}  // namespace gb

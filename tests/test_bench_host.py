@@ -1,0 +1,94 @@
+"""Host-side logic of bench.py: workload bookkeeping, the whole-job value,
+max-over-ranks timing on a 2-rank gloo group (the multi-GPU path is
+replicas only), clock-sample parsing and the reference (CPU oracle) arm."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_op_list_is_the_sweep():
+    ops = bench.op_list()
+    assert len(ops) == 18
+    assert len({o[0] for o in ops}) == 18
+    kinds = [o[1] for o in ops]
+    assert kinds.count("gemv") == 12 and kinds.count("dot") == 2 and kinds.count("ger") == 4
+
+
+@pytest.mark.parametrize("kind,dt,m,n,want", [
+    ("gemv", "f64", 4096, 4096, 134_316_032),
+    ("gemv", "f32", 16384, 16384, 1_073_938_432),
+    ("gemv", "f64", 16384, 16384, 2_147_876_864),
+    ("gemv", "f32", 1048576, 64, 276_824_320),
+    ("gemv", "f64", 1048576, 64, 553_648_640),
+    ("gemv", "f32", 64, 1048576, 272_630_272),
+    ("gemv", "f64", 64, 1048576, 545_260_544),
+    ("ger", "f32", 16384, 16384, 2_147_614_720),
+    ("ger", "f64", 16384, 16384, 4_295_229_440),
+    ("dot", "f64", 1, 1 << 28, 8 * (2 * (1 << 28) + 2)),
+])
+def test_algorithmic_bytes(kind, dt, m, n, want):
+    assert bench.alg_bytes(kind, dt, m, n) == want
+
+
+def test_whole_job_value():
+    assert bench.whole_job_value(1e9, 10, 1, 2.0) == pytest.approx(5.0)
+    assert bench.whole_job_value(1e9, 10, 4, 2.0) == pytest.approx(20.0)
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench as b
+    w, r = b.init_dist("gloo")
+    b.barrier()
+    mx = b.max_over_ranks(1.5 + r)
+    out.put((r, w, mx))
+    import torch.distributed as dist
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_two_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 29500 + os.getpid() % 1000
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == [(0, 2, 2.5), (1, 2, 2.5)]
+
+
+def test_clock_summary_parsing():
+    cs = bench.ClockSampler(0)
+    row = lambda mhz, pc: ["2026/01/01", str(mhz), "2070", "900", "0x0", "Not Active",
+                           "Not Active", "Not Active", pc]
+    cs.samples = [(10.0, row(1900, "Not Active")), (11.0, row(1950, "Active")),
+                  (12.0, row(2000, "Not Active")), (13.0, row(1000, "Not Active"))]
+    s = cs.summary(9.5, 12.5)
+    assert s["sm_mhz"] == 1950 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
+
+
+def test_reference_arm_prints_contract_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                       timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "impl", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "cpu_baseline", "e2e", "config"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["unit"] == "GB/s" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
