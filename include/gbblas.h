@@ -160,6 +160,30 @@ int gb_dger(int layout, int64_t m, int64_t n, double alpha, const double *x, con
 int gb_sger(int layout, int64_t m, int64_t n, float alpha, const float *x, const float *y,
             float *C, int64_t ldc, gb_stream stream);
 
+/* GEMV without allocation.  The paper has no counterpart: this entry point
+   exists for callers that cannot allocate device memory (code running where
+   cudaMalloc is not allowed, such as a host callback, or a runtime that owns
+   the whole device heap) and so cannot pass the workspace of gb_dgemv.
+   It computes exactly what gb_dgemv computes, with the same kernels, but its
+   split sums use a scratch array of GB_NOALLOC_SCRATCH_BYTES compiled into
+   the library, which every GPU that loads the library holds until the
+   process exits.  It calls no cudaMalloc, cudaFree or other allocating
+   routine.
+     Arguments 1-8 as for gb_dgemv; stream is argument 9.
+     Returns what gb_dgemv returns, and GB_ERR_WORKSPACE (nothing enqueued)
+     when the call would need more than GB_NOALLOC_SCRATCH_BYTES of scratch,
+     that is when gb_workspace_bytes(GB_OP_GEMV, GB_F64, layout, m, n)
+     exceeds it.
+   The first call on a device looks up the array's device address with that
+   device current (cudaGetSymbolAddress); make that first call before any
+   stream capture.  Each call first zeroes the array's counters on `stream`
+   (cudaMemsetAsync), because the array keeps the previous call's contents.
+   All calls share the one array: calls that overlap on the GPU (different
+   streams, different threads) race and give wrong results; serialise them. */
+#define GB_NOALLOC_SCRATCH_BYTES ((size_t)256 << 10)  /* 256 KiB */
+int gb_dgemv_noalloc(int layout, int64_t m, int64_t n, double alpha, const double *A,
+                     int64_t lda, const double *x, double *c, gb_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,7 +56,9 @@ def _load() -> ctypes.CDLL:
     lib.gb_sdot.argtypes = [I64, P, P, P, P, SZ, P]
     lib.gb_dger.argtypes = [I, I64, I64, D, P, P, P, I64, P]
     lib.gb_sger.argtypes = [I, I64, I64, F, P, P, P, I64, P]
-    for name in ("gb_dgemv", "gb_sgemv", "gb_ddot", "gb_sdot", "gb_dger", "gb_sger"):
+    lib.gb_dgemv_noalloc.argtypes = [I, I64, I64, D, P, I64, P, P, P]
+    for name in ("gb_dgemv", "gb_sgemv", "gb_ddot", "gb_sdot", "gb_dger", "gb_sger",
+                 "gb_dgemv_noalloc"):
         getattr(lib, name).restype = I
     return lib
 
@@ -65,7 +67,8 @@ _lib = _load()
 
 # Every symbol the header declares (checked by the tests against include/gbblas.h).
 EXPORTS = ("gb_version", "gb_status_string", "gb_workspace_bytes", "gb_workspace_init",
-           "gb_dgemv", "gb_sgemv", "gb_ddot", "gb_sdot", "gb_dger", "gb_sger")
+           "gb_dgemv", "gb_sgemv", "gb_ddot", "gb_sdot", "gb_dger", "gb_sger",
+           "gb_dgemv_noalloc")
 
 
 def lib() -> ctypes.CDLL:
@@ -134,6 +137,13 @@ def gb_dger(layout, m, n, alpha, x, y, C, ldc, stream=None) -> int:
 
 def gb_sger(layout, m, n, alpha, x, y, C, ldc, stream=None) -> int:
     return _lib.gb_sger(layout, m, n, alpha, _ptr(x), _ptr(y), _ptr(C), ldc, _stream(stream))
+
+
+def gb_dgemv_noalloc(layout, m, n, alpha, A, lda, x, c, stream=None) -> int:
+    """gb_dgemv with the library's own scratch array instead of a workspace,
+    for callers that cannot allocate device memory."""
+    return _lib.gb_dgemv_noalloc(layout, m, n, alpha, _ptr(A), lda, _ptr(x), _ptr(c),
+                                 _stream(stream))
 
 
 # ---------------------------------------------------------- convenience ----

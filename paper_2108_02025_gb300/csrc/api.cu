@@ -399,3 +399,81 @@ int gb_sger(int layout, int64_t m, int64_t n, float alpha, const float* x, const
 }
 
 }  // extern "C"
+
+// ------------------------------------------------- GEMV without allocation ---
+//
+// gb_dgemv_noalloc: the FP64 GEMV of gb_dgemv for callers that cannot call
+// cudaMalloc or take memory from an allocator (code inside a host callback
+// or a custom runtime that owns the device heap, for example).  Its split
+// sums use a scratch array compiled into this library instead of a
+// caller-supplied workspace.
+
+namespace gb {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(256) << 10;  // 256 KiB on every GPU that loads us
+constexpr int kNoAllocMaxDevices = 64;
+
+// Lives on each device for the lifetime of the process.  In host code this
+// name is only a stand-in: its device address comes from
+// cudaGetSymbolAddress (noalloc_scratch below).
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of the scratch array on the current device, looked up once
+// per device (with that device current) and cached; nullptr on failure.
+void* noalloc_scratch() {
+  static std::mutex mu;
+  static void* addr[kNoAllocMaxDevices] = {};
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (addr[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return nullptr;
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
+// Bytes at the start of the workspace that hold arrival counters (they must
+// be zero when a call starts), for either pointer-alignment variant.
+size_t noalloc_ticket_bytes(int layout, int64_t m, int64_t n) {
+  size_t b = 0;
+  for (int vec = 0; vec < 2; ++vec) {
+    const SplitShape s = layout == GB_ROW_MAJOR ? row_shape(8, vec, m, n).sp : col_shape(8, vec, m, n).sp;
+    if (s.S <= 1) continue;
+    const size_t t = ((size_t)s.tiles * (s.NG + 1) * sizeof(unsigned) + 255) / 256 * 256;
+    if (t > b) b = t;
+  }
+  return b;
+}
+
+}  // namespace
+}  // namespace gb
+
+extern "C" int gb_dgemv_noalloc(int layout, int64_t m, int64_t n, double alpha, const double* A,
+                                int64_t lda, const double* x, double* c, gb_stream stream) {
+  using namespace gb;
+  // Argument checks in the order of gb_dgemv, so that an invalid call
+  // returns the same status and enqueues nothing.
+  const bool shape_ok = (layout == GB_ROW_MAJOR || layout == GB_COL_MAJOR) && m >= 0 && n >= 0 &&
+                        lda >= (layout == GB_ROW_MAJOR ? (n > 1 ? n : 1) : (m > 1 ? m : 1));
+  if (!shape_ok || m == 0 || n == 0 || alpha == 0.0 || !A || !x || !c)
+    return gemv<double>(layout, m, n, alpha, A, lda, x, c, nullptr, 0, stream);
+  const unsigned __int128 cb = (unsigned __int128)m * sizeof(double);
+  if (overlap(c, cb, A, matrix_bytes(layout, m, n, lda, sizeof(double))) ||
+      overlap(c, cb, x, (unsigned __int128)n * sizeof(double)))
+    return -8;
+  const size_t need = gemv_ws(sizeof(double), layout, m, n);
+  if (need > kNoAllocScratchBytes) return GB_ERR_WORKSPACE;  // the built-in scratch is too small
+  void* ws = nullptr;
+  if (need > 0) {
+    ws = noalloc_scratch();
+    if (ws == nullptr) return GB_ERR_CUDA;
+    // The array keeps the previous call's contents: zero the counters.
+    const size_t tb = noalloc_ticket_bytes(layout, m, n);
+    if (tb > 0 && cudaMemsetAsync(ws, 0, tb, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+      return GB_ERR_CUDA;
+  }
+  return gemv<double>(layout, m, n, alpha, A, lda, x, c, ws, need, stream);
+}
