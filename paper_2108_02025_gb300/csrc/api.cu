@@ -12,8 +12,10 @@
 namespace gb {
 namespace {
 
-constexpr int64_t kTargetUnits = 608;   // one wave of 4 blocks on each of 152 SMs
-constexpr int kMaxSplits = 512;
+// Warps resident at once in the pipelined GEMV kernels on GB300: 152 SMs x
+// 2 blocks x 8 warps (shared memory allows two blocks per SM).
+constexpr int64_t kWaveWarps = 2432;
+constexpr int kMaxSplits = 4096;
 constexpr int64_t kDotSmall = 16384;    // up to here DOT is one block (Alg. 3)
 constexpr int64_t kDotBlocks = 608;     // large DOT: at most this many blocks (Alg. 4)
 constexpr int kDotPack = 4;             // packs per thread per step in the DOT kernel
@@ -44,76 +46,178 @@ inline unsigned __int128 matrix_bytes(int layout, int64_t m, int64_t n, int64_t 
 // ---------------------------------------------------------------- plans ---
 
 struct SplitShape {
-  int S, NG;
-  int64_t kc, tiles;
+  int S, G, NG;
+  int64_t kc, items;
 };
+
+inline size_t ticket_bytes(const SplitShape& s) {
+  return ((size_t)s.items * (s.NG + 1) * sizeof(unsigned) + 255) / 256 * 256;
+}
 
 inline size_t split_bytes(const SplitShape& s, int64_t m) {
   if (s.S <= 1) return 0;
-  const size_t tick = (size_t)s.tiles * (s.NG + 1) * sizeof(unsigned);
-  const size_t tick_pad = (tick + 255) / 256 * 256;
-  return tick_pad + (size_t)s.S * m * sizeof(double) + (s.NG > 1 ? (size_t)s.NG * m * sizeof(double) : 0);
+  return ticket_bytes(s) + (size_t)s.S * m * sizeof(double) +
+         (s.NG > 1 ? (size_t)s.NG * m * sizeof(double) : 0);
 }
 
 inline Split split_view(const SplitShape& s, int64_t m, void* ws) {
-  Split sp{s.S, s.NG, m, nullptr, nullptr, nullptr};
+  Split sp{s.S, s.G, s.NG, m, nullptr, nullptr, nullptr};
   if (s.S <= 1) return sp;
-  const size_t tick = (size_t)s.tiles * (s.NG + 1) * sizeof(unsigned);
-  const size_t tick_pad = (tick + 255) / 256 * 256;
   char* base = static_cast<char*>(ws);
   sp.tickets = reinterpret_cast<unsigned*>(base);
-  sp.part = reinterpret_cast<double*>(base + tick_pad);
+  sp.part = reinterpret_cast<double*>(base + ticket_bytes(s));
   sp.part2 = s.NG > 1 ? sp.part + (size_t)s.S * m : nullptr;
   return sp;
 }
 
-// Number of chunks for `tiles` row tiles over a summed index of length n
-// whose chunks must hold at least `min_kc` indices and be multiples of
-// `quantum`.  Depends only on the shape.
-inline SplitShape choose_split(int64_t tiles, int64_t n, int64_t min_kc, int64_t quantum) {
-  SplitShape s{1, 1, n > 0 ? n : 1, tiles};
-  if (tiles >= kTargetUnits / 2 || n <= min_kc) return s;
-  int64_t S = kTargetUnits / tiles;
-  if (S > kMaxSplits) S = kMaxSplits;
-  const int64_t smax = n / min_kc;
-  if (S > smax) S = smax;
-  if (S < 2) return s;
-  int64_t kc = cdiv(cdiv(n, S), quantum) * quantum;
-  S = cdiv(n, kc);
+inline int64_t isqrt_ceil(int64_t v) {
+  int64_t r = 1;
+  while (r * r < v) ++r;
+  return r;
+}
+
+// Number of chunks of the summed index (length n, element size e) for
+// `items` row items.  The items * S warp work items are spread over the
+// kWaveWarps warps that fit on the GPU at once: S is the smallest split count
+// whose last wave is at least 95% full (else the fullest), with chunks of at
+// least `min_kc` indices (multiples of `quantum`) and the partial sums'
+// traffic (16 bytes per row per chunk) under 1% of the matrix's.  Depends
+// only on the shape.
+inline SplitShape choose_split(int64_t items, int64_t n, int64_t min_kc, int64_t quantum, size_t e) {
+  SplitShape s{1, 1, 1, n > 0 ? n : 1, items};
+  int64_t smax = kMaxSplits;
+  if (smax > n / min_kc) smax = n / min_kc;
+  if (smax > n * (int64_t)e / 1600) smax = n * (int64_t)e / 1600;
+  auto fill = [&](int64_t S) {
+    const int64_t u = items * S;
+    return (double)u / (double)(cdiv(u, kWaveWarps) * kWaveWarps);
+  };
+  int64_t best = 1;
+  double best_fill = fill(1);
+  if (best_fill < 0.95) {
+    for (int64_t S = 2; S <= smax; ++S) {
+      const double f = fill(S);
+      if (f > best_fill + 1e-9) { best = S; best_fill = f; }
+      if (f >= 0.95) break;
+    }
+  }
+  if (best < 2) return s;
+  const int64_t kc = cdiv(cdiv(n, best), quantum) * quantum;
+  const int64_t S = cdiv(n, kc);
   if (S < 2) return s;
   s.S = (int)S;
-  s.NG = (int)cdiv(S, kGroup);
+  s.G = S <= 32 ? (int)S : (int)isqrt_ceil(S);  // one level up to 32 partials
+  s.NG = (int)cdiv(S, s.G);
+  s.kc = kc;
+  return s;
+}
+
+inline int64_t pow2_floor(int64_t v) {
+  int64_t p = 1;
+  while (p * 2 <= v) p <<= 1;
+  return p;
+}
+
+// Blocks resident at once in the block-streaming GEMV kernels on GB300: 152
+// SMs x 4 blocks of 256 threads.
+constexpr int64_t kWaveBlocks = 608;
+
+// Split count for the block-streaming kernels, whose blocks take equal
+// consecutive ranges of `items * S` units: the smallest S giving at least
+// 4 units per block with the busiest block at most 5% above the average,
+// else the most even S (units below one per block are penalised).  Chunks
+// hold at least `min_kc` indices (multiples of `quantum`); the partials'
+// traffic (16 bytes per row per chunk) stays under 1% of the matrix's.
+// Depends only on the shape.
+inline SplitShape block_split(int64_t items, int64_t n, int64_t min_kc, int64_t quantum, size_t e) {
+  SplitShape s{1, 1, 1, n > 0 ? n : 1, items};
+  int64_t smax = kMaxSplits;
+  if (smax > n / min_kc) smax = n / min_kc;
+  if (smax > n * (int64_t)e / 1600) smax = n * (int64_t)e / 1600;
+  auto even = [&](int64_t S) {
+    const double u = (double)(items * S) / kWaveBlocks;  // units per block, average
+    const double busiest = (double)cdiv(items * S, kWaveBlocks);
+    return (u / busiest) * (u < 1.0 ? u : 1.0);
+  };
+  if (items >= 4 * kWaveBlocks || smax < 2) return s;
+  int64_t best = 1;
+  double best_even = even(1);
+  for (int64_t S = 2; S <= smax; ++S) {
+    const double ev = even(S);
+    if (items * S >= 4 * kWaveBlocks && ev >= 0.95) { best = S; break; }
+    if (ev > best_even + 1e-9) { best = S; best_even = ev; }
+  }
+  if (best < 2) return s;
+  const int64_t kc = cdiv(cdiv(n, best), quantum) * quantum;
+  const int64_t S = cdiv(n, kc);
+  if (S < 2) return s;
+  s.S = (int)S;
+  s.G = S <= 32 ? (int)S : (int)isqrt_ceil(S);
+  s.NG = (int)cdiv(S, s.G);
   s.kc = kc;
   return s;
 }
 
 struct RowShape {
-  int lpr, rw;
+  GemvPlan::Kind kind;
+  int lpr;
+  bool long_chain;
   SplitShape sp;
 };
 
 inline RowShape row_shape(size_t e, bool vec, int64_t m, int64_t n) {
   const int64_t V = vec ? 16 / (int64_t)e : 1;
-  RowShape r;
+  RowShape r{};
   const int64_t packs = cdiv(n, V);
-  r.lpr = (int)pow2_at_least(packs, 32);
-  r.rw = packs <= 2 * 32 ? 8 : 4;
-  const int64_t rows = (256 / r.lpr) * r.rw;
-  r.sp = choose_split(cdiv(m, rows), n, r.lpr * V * 2 * 4, r.lpr * V);
+  if (vec && packs <= 256) {  // short rows: lane groups of up to 8 packs each, no split
+    r.kind = GemvPlan::kRowShort;
+    r.lpr = (int)pow2_at_least(cdiv(packs, 8), 32);
+    r.sp = SplitShape{1, 1, 1, n, cdiv(m, 256 / r.lpr)};
+    return r;
+  }
+  if (vec) {  // long rows: blocks stream (row, chunk) units; one counter per row
+    r.kind = GemvPlan::kRowLong;
+    const int64_t quantum = 256 * V;
+    SplitShape s = block_split(m, n, quantum * kRowLongU, quantum, e);
+    s.G = s.S;   // the long-row kernel sums a row's S partials in one level
+    s.NG = 1;
+    r.sp = s;
+    r.long_chain = e == 4 && cdiv(s.kc, 256 * V) * V > 64;
+    return r;
+  }
+  r.kind = GemvPlan::kRowScalar;  // misaligned operands
+  int64_t lpr = pow2_floor(packs / 8 > 0 ? packs / 8 : 1);
+  r.lpr = (int)(lpr > 32 ? 32 : lpr);
+  const int64_t rows = (32 / r.lpr) * kRowScalarRW;
+  r.sp = choose_split(cdiv(m, rows), n, r.lpr * 8, 1, e);
   return r;
 }
 
 struct ColShape {
-  int tx;
+  int txw;
+  bool long_chain;
   SplitShape sp;
 };
+
+constexpr int kColU = 8;  // columns unrolled, misaligned column-major kernel (gemv_col.cu)
 
 inline ColShape col_shape(size_t e, bool vec, int64_t m, int64_t n) {
   const int64_t V = vec ? 16 / (int64_t)e : 1;
   ColShape c;
-  c.tx = (int)pow2_at_least(cdiv(m, V), 64);
-  const int64_t ty = 256 / c.tx;
-  c.sp = choose_split(cdiv(m, c.tx * V), n, ty * 4 * 4, 1);
+  if (vec) {  // block tiles of tx*V rows; tx threads along the rows, 256/tx along the columns
+    const int64_t tx = pow2_at_least(cdiv(m, V), 64);
+    const int64_t ty = 256 / tx;
+    c.txw = (int)tx;
+    c.sp = block_split(cdiv(m, tx * V), n, ty * kColTileU, 1, e);
+    c.long_chain = e == 4 && cdiv(c.sp.kc, ty) > 64;
+    return c;
+  }
+  // misaligned operands: warp items; at most 32 row lanes, no more than the rows need
+  const int64_t txw = pow2_at_least(cdiv(m, V), 32);
+  const int64_t tyw = 32 / txw;
+  c.txw = (int)txw;
+  c.sp = choose_split(cdiv(m, txw * V), n, tyw * kColU * 2, 1, e);
+  c.long_chain = e == 4 && cdiv(c.sp.kc, tyw) > 64;
   return c;
 }
 
@@ -224,17 +328,19 @@ int gemv(int layout, int64_t m, int64_t n, T alpha, const T* A, int64_t lda, con
   SplitShape s;
   if (layout == GB_ROW_MAJOR) {
     const RowShape r = row_shape(e, vec, m, n);
+    p.kind = r.kind;
     p.lpr = r.lpr;
-    p.rw = r.rw;
+    p.long_chain = r.long_chain;
     s = r.sp;
   } else {
     const ColShape cs = col_shape(e, vec, m, n);
-    p.tx = cs.tx;
+    p.kind = GemvPlan::kCol;
+    p.txw = cs.txw;
+    p.long_chain = cs.long_chain;
     s = cs.sp;
   }
   p.kc = s.kc;
-  p.tiles = s.tiles;
-  p.units = s.tiles * s.S;
+  p.units = s.items * s.S;
   p.split = split_view(s, m, ws);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (layout == GB_ROW_MAJOR) gemv_row_launch<T>(a, p, st);
@@ -325,6 +431,25 @@ int grid_size(const void* kernel, int64_t units, size_t smem) {
     }
   }
   return (int)(units < blocks ? (units > 0 ? units : 1) : blocks);
+}
+
+bool allow_smem(const void* kernel, size_t bytes) {
+  struct Entry {
+    const void* k;
+    int dev;
+  };
+  static Entry done[256];
+  static int used = 0;
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  for (int i = 0; i < used; ++i)
+    if (done[i].k == kernel && done[i].dev == dev) return true;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+    return false;
+  if (used < 256) done[used++] = Entry{kernel, dev};
+  return true;
 }
 
 }  // namespace gb
@@ -442,7 +567,7 @@ size_t noalloc_ticket_bytes(int layout, int64_t m, int64_t n) {
   for (int vec = 0; vec < 2; ++vec) {
     const SplitShape s = layout == GB_ROW_MAJOR ? row_shape(8, vec, m, n).sp : col_shape(8, vec, m, n).sp;
     if (s.S <= 1) continue;
-    const size_t t = ((size_t)s.tiles * (s.NG + 1) * sizeof(unsigned) + 255) / 256 * 256;
+    const size_t t = ticket_bytes(s);
     if (t > b) b = t;
   }
   return b;

@@ -59,6 +59,43 @@ __device__ __forceinline__ void st_stream(T* p, const Pack<T, V>& r) {
   }
 }
 
+// ---- asynchronous global -> shared copies (cp.async), 16 bytes per lane.
+// Each lane copies, waits for and reads back only its own slots, so no
+// barrier is needed between lanes; the hardware tracks completion per thread.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+// Streamed data: bypass L1 (.cg).
+__device__ __forceinline__ void cp_async_cg16(unsigned dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+// Reused data (x): through L1 (.ca).
+__device__ __forceinline__ void cp_async_ca16(unsigned dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_ca4(unsigned dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename T, int V>
+__device__ __forceinline__ Pack<T, V> lds_pack(const unsigned char* p) {
+  Pack<T, V> r;
+  if constexpr (sizeof(T) == 4 && V == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
+  } else {
+    static_assert(sizeof(T) == 8 && V == 2, "16-byte packs only");
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    r.v[0] = q.x; r.v[1] = q.y;
+  }
+  return r;
+}
+
 // Correctly rounded fma in the element type.
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -74,10 +111,20 @@ __device__ __forceinline__ double group_sum(double v) {
   return v;
 }
 
-// c_i <- c_i + alpha * s, computed in FP64 and rounded once to T.
-template <typename T>
-__device__ __forceinline__ T update(T c0, T alpha, double s) {
-  return (T)__fma_rn((double)alpha, s, (double)c0);
+// c_i <- c_i + alpha * s in the element type: one fma.  (FP32 paths avoid
+// FP64 instructions altogether: on this GPU every FP64 warp instruction,
+// even with one active lane, occupies the small FP64 pipe.)
+__device__ __forceinline__ float update(float c0, float alpha, float s) { return __fmaf_rn(alpha, s, c0); }
+__device__ __forceinline__ double update(double c0, double alpha, double s) { return __fma_rn(alpha, s, c0); }
+// The same from an FP64 partial sum (split sums are combined in FP64).
+__device__ __forceinline__ float update_from(float c0, float alpha, double s) { return __fmaf_rn(alpha, (float)s, c0); }
+__device__ __forceinline__ double update_from(double c0, double alpha, double s) { return __fma_rn(alpha, s, c0); }
+
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
 }
 
 // Block-wide sum of one double per thread, in a fixed order (warp butterfly,
@@ -114,22 +161,80 @@ __device__ __forceinline__ bool arrive_last(unsigned* ticket, unsigned expected,
   return last;
 }
 
-// Sum `count` partial values per output row, value q of row r being
-// src[q * stride + row0 + r], in index order q = 0, 1, ... (cut into slices
-// so that all threads load at once; slices are combined in slice order
-// through shared memory), then hand (row, sum) to `sink` once per row.
-// `red` must hold kThreads doubles.  Synchronises the block.
+// Sum over aligned groups of W lanes in the element type (FP32 partials
+// stay on the FP32 pipe), same fixed butterfly order as group_sum.
+template <int W>
+__device__ __forceinline__ float group_sum_f(float v) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Arrival counter of one output tile, for a warp that has written its
+// partial sums (every lane that wrote calls this with the whole warp).
+// Returns true in the warp that arrived last; the fence/atomic pair makes
+// the partials of every earlier warp visible to it.
+__device__ __forceinline__ bool warp_arrive_last(unsigned* ticket, unsigned expected) {
+  __threadfence();
+  __syncwarp();
+  unsigned prev = 0;
+  if ((threadIdx.x & 31) == 0) prev = atomicAdd(ticket, 1u);
+  prev = __shfl_sync(0xffffffffu, prev, 0);
+  const bool last = prev == expected - 1;
+  if (last) __threadfence();
+  return last;
+}
+
+// Warp-wide sum, for each of `rows` outputs, of `count` partials: value q
+// of row r is src[q * stride + row0 + r].  The warp works on up to 32/P rows
+// at once with P lanes per row; lane k of a row adds q = k, k+P, ... in
+// order, and the P lanes are combined by the fixed butterfly.  `sink(row, v)`
+// runs in the first lane of each row's group.
+template <int P, typename Sink>
+__device__ __forceinline__ void warp_sum_rows_p(const double* src, int64_t stride, int count,
+                                                int64_t row0, int rows, Sink& sink) {
+  const int lane = threadIdx.x & 31;
+  const int k = lane % P;
+  for (int rb = 0; rb < rows; rb += 32 / P) {
+    const int r = rb + lane / P;
+    double s = 0.0;
+    if (r < rows)
+      for (int q = k; q < count; q += P) s = __dadd_rn(s, __ldcg(src + (int64_t)q * stride + row0 + r));
+    s = group_sum<P>(s);
+    if (k == 0 && r < rows) sink(row0 + r, s);
+  }
+}
+
 template <typename Sink>
-__device__ void sum_rows(const double* src, int64_t stride, int count, int64_t row0, int64_t rows,
-                         double* red, Sink sink) {
+__device__ __forceinline__ void warp_sum_rows(const double* src, int64_t stride, int count,
+                                              int64_t row0, int rows, Sink sink) {
+  // lanes per row: as many as fit when all rows are handled in one pass
+  const int per = rows >= 32 ? 1 : 32 / rows;
+  if (per >= 32) warp_sum_rows_p<32>(src, stride, count, row0, rows, sink);
+  else if (per >= 16) warp_sum_rows_p<16>(src, stride, count, row0, rows, sink);
+  else if (per >= 8) warp_sum_rows_p<8>(src, stride, count, row0, rows, sink);
+  else if (per >= 4) warp_sum_rows_p<4>(src, stride, count, row0, rows, sink);
+  else if (per >= 2) warp_sum_rows_p<2>(src, stride, count, row0, rows, sink);
+  else warp_sum_rows_p<1>(src, stride, count, row0, rows, sink);
+}
+
+// Block-wide sum, for each of `rows` outputs, of `count` partials: value q
+// of row r is src[q * stride + row0 + r].  The 256 threads are cut into
+// slices of the partials so that all of them load at once: slice k adds its
+// partials in index order, the slices are added in slice order through
+// shared memory, and `sink(row, v)` runs once per row.  `red` holds 256
+// doubles.  Synchronises the block.
+template <typename Sink>
+__device__ void block_sum_rows(const double* src, int64_t stride, int count, int64_t row0,
+                               int64_t rows, double* red, Sink sink) {
   int nslice = kThreads / (int)(rows < kThreads ? rows : kThreads);
   if (nslice > count) nslice = count;
   const int per = (count + nslice - 1) / nslice;
-  const int64_t crow = kThreads / nslice;  // rows handled per pass
+  const int64_t crow = kThreads / nslice;  // rows per pass
   for (int64_t base = 0; base < rows; base += crow) {
     const int64_t r = base + threadIdx.x % crow;
     const int slice = (int)(threadIdx.x / crow);
-    double s = 0.0;
+    double acc = 0.0;
     if (slice < nslice && r < rows) {
       const int q0 = slice * per;
       const int q1 = q0 + per < count ? q0 + per : count;
@@ -140,47 +245,79 @@ __device__ void sum_rows(const double* src, int64_t stride, int count, int64_t r
 #pragma unroll
         for (int k = 0; k < 8; ++k) v[k] = __ldcg(p + (int64_t)(q + k) * stride);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) s = __dadd_rn(s, v[k]);
+        for (int k = 0; k < 8; ++k) acc = __dadd_rn(acc, v[k]);
       }
-      for (; q < q1; ++q) s = __dadd_rn(s, __ldcg(p + (int64_t)q * stride));
+      for (; q < q1; ++q) acc = __dadd_rn(acc, __ldcg(p + (int64_t)q * stride));
     }
-    red[threadIdx.x] = s;
+    __syncthreads();
+    red[threadIdx.x] = acc;
     __syncthreads();
     if (threadIdx.x < crow && base + threadIdx.x < rows) {
       double t = 0.0;
       for (int k = 0; k < nslice; ++k) t = __dadd_rn(t, red[k * crow + threadIdx.x]);
       sink(row0 + base + threadIdx.x, t);
     }
-    __syncthreads();
   }
+  __syncthreads();
 }
 
-// Called by every thread of the block that wrote partial `s` of the rows
-// [row0, row0 + rows) of tile `tile`.  The last block of each group sums the
-// group; the last group sums the groups and applies c <- c + alpha*sum.
-// Every counter is back at zero when the call's last block finishes.
+// Final step of a split sum for a block that has written partial `s` of the
+// rows [row0, row0 + rows) of tile `tile` (called by every thread).  The
+// last block of each group of sp.G splits sums the group, the last group
+// sums the groups and applies c <- c + alpha*sum; counters return to zero.
 template <typename T>
-__device__ void split_finish(const Split& sp, int64_t tile, int s, int64_t row0, int64_t rows,
-                             T* c, T alpha, double* red, int* flag) {
-  const int g = s / kGroup;
-  const int gsize = (g + 1) * kGroup <= sp.S ? kGroup : sp.S - g * kGroup;
+__device__ __noinline__ void block_split_finish(const Split& sp, int64_t tile, int s, int64_t row0,
+                                                int64_t rows, T* c, T alpha, double* red, int* flag) {
+  const int g = s / sp.G;
+  const int gsize = (g + 1) * sp.G <= sp.S ? sp.G : sp.S - g * sp.G;
   unsigned* t1 = sp.tickets + tile * (sp.NG + 1) + g;
   unsigned* t2 = sp.tickets + tile * (sp.NG + 1) + sp.NG;
   if (!arrive_last(t1, (unsigned)gsize, flag)) return;
-  const double* src = sp.part + (int64_t)g * kGroup * sp.m;
+  const double* src = sp.part + (int64_t)g * sp.G * sp.m;
   if (sp.NG == 1) {
-    sum_rows(src, sp.m, gsize, row0, rows, red,
-             [&](int64_t row, double v) { c[row] = update(c[row], alpha, v); });
+    block_sum_rows(src, sp.m, gsize, row0, rows, red,
+                   [&](int64_t row, double v) { c[row] = update_from(c[row], alpha, v); });
     if (threadIdx.x == 0) *t1 = 0u;
     return;
   }
-  sum_rows(src, sp.m, gsize, row0, rows, red,
-           [&](int64_t row, double v) { sp.part2[(int64_t)g * sp.m + row] = v; });
+  block_sum_rows(src, sp.m, gsize, row0, rows, red,
+                 [&](int64_t row, double v) { sp.part2[(int64_t)g * sp.m + row] = v; });
   if (threadIdx.x == 0) *t1 = 0u;
   if (!arrive_last(t2, (unsigned)sp.NG, flag)) return;
-  sum_rows(sp.part2, sp.m, sp.NG, row0, rows, red,
-           [&](int64_t row, double v) { c[row] = update(c[row], alpha, v); });
+  block_sum_rows(sp.part2, sp.m, sp.NG, row0, rows, red,
+                 [&](int64_t row, double v) { c[row] = update_from(c[row], alpha, v); });
   if (threadIdx.x == 0) *t2 = 0u;
+}
+
+// Final step of a split sum, run by the warp that wrote partial `s` of rows
+// [row0, row0 + rows) of row item `item`.  The S partials of a row are
+// combined in groups of sp.G consecutive splits by the last warp to arrive
+// in each group, then across the NG groups by the last group; each sum is in
+// index order, and every counter is back at zero when the call's last warp
+// finishes.  Workspace layout: see gb_split.h.
+template <typename T>
+__device__ __noinline__ void warp_split_finish(const Split& sp, int64_t item, int s, int64_t row0, int rows,
+                                  T* c, T alpha) {
+  const int g = s / sp.G;
+  const int gsize = (g + 1) * sp.G <= sp.S ? sp.G : sp.S - g * sp.G;
+  unsigned* t1 = sp.tickets + item * (sp.NG + 1) + g;
+  unsigned* t2 = sp.tickets + item * (sp.NG + 1) + sp.NG;
+  if (!warp_arrive_last(t1, (unsigned)gsize)) return;
+  const double* src = sp.part + (int64_t)g * sp.G * sp.m;
+  const bool lane0 = (threadIdx.x & 31) == 0;
+  if (sp.NG == 1) {
+    warp_sum_rows(src, sp.m, gsize, row0, rows,
+                  [&](int64_t row, double v) { c[row] = update_from(c[row], alpha, v); });
+    if (lane0) *t1 = 0u;
+    return;
+  }
+  warp_sum_rows(src, sp.m, gsize, row0, rows,
+                [&](int64_t row, double v) { sp.part2[(int64_t)g * sp.m + row] = v; });
+  if (lane0) *t1 = 0u;
+  if (!warp_arrive_last(t2, (unsigned)sp.NG)) return;
+  warp_sum_rows(sp.part2, sp.m, sp.NG, row0, rows,
+                [&](int64_t row, double v) { c[row] = update_from(c[row], alpha, v); });
+  if (lane0) *t2 = 0u;
 }
 
 }  // namespace gb

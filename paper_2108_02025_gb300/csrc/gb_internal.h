@@ -21,18 +21,24 @@ struct GemvArgs {
   T* c;
 };
 
-// How one GEMV is cut into work units.  Depends only on (dtype, layout, m, n)
-// and pointer alignment (which selects the 16-byte or the scalar variant;
-// both sum in the same per-lane order only for the same variant).
+// Tuning constants shared by the planner (api.cu) and the kernels.
+constexpr int kRowLongU = 4;     // packs in flight per thread, long-row kernel
+constexpr int kRowScalarRW = 4;  // rows per lane group, misaligned row-major kernel
+constexpr int kColTileU = 8;     // columns in flight per thread, column-major tile kernel
+
+// How one GEMV is cut into work.  The kernel, the split S and the per-thread
+// summation order depend only on (dtype, layout, m, n) and on the pointer
+// alignment (which selects the 16-byte or the scalar variant).
 struct GemvPlan {
-  bool vec;        // 16-byte packs (A, x 16-byte aligned and lda a multiple of the pack)
-  int lpr;         // row-major: lanes per row (1..32)
-  int rw;          // row-major: rows per lane group
-  int tx;          // column-major: threads along the rows of a tile
-  int64_t kc;      // columns per chunk
-  int64_t tiles;   // row tiles
-  int64_t units;   // tiles * S
-  Split split;     // S chunks of the summed index (S = 1: no split) and their workspace
+  enum Kind { kRowLong, kRowShort, kRowScalar, kCol };
+  Kind kind;
+  bool vec;         // 16-byte packs (A, x 16-byte aligned and lda a multiple of the pack)
+  bool long_chain;  // FP32 only: a thread sums more than 64 products of one row
+  int lpr;          // row-major short / scalar: lanes per row (1..32)
+  int txw;          // column-major: lanes along the rows of a warp item (1..32)
+  int64_t kc;       // columns per chunk
+  int64_t units;    // work units (kRowLong: m * S; warp kernels: items * S)
+  Split split;      // S chunks of the summed index (S = 1: no split) and their workspace
 };
 
 template <typename T>
@@ -70,6 +76,10 @@ struct GerPlan {
 // Blocks to launch for `units` independent work units: every SM filled to
 // the kernel's occupancy, never more blocks than units.
 int grid_size(const void* kernel, int64_t units, size_t smem = 0);
+
+// Allow `kernel` `bytes` of dynamic shared memory on the current device
+// (once per kernel and device).  Returns false if the device refuses.
+bool allow_smem(const void* kernel, size_t bytes);
 
 template <typename T>
 int gemv_row_launch(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st);

@@ -2,129 +2,306 @@
 //
 // Alg. 1 of the paper (Sec. 4.1) blocks rows by m_c, columns by n_c and
 // updates a short run of c, c(i_r : i_r + m_r), from a block of A and the
-// matching block of x (its micro-kernel).  Here a block tile is TX*V rows
-// (each thread owns V consecutive rows, moved as one 16-byte pack per
-// column: the m_r of the micro-kernel) by a chunk of KC columns (n_c),
-// walked by TY = 256/TX column lanes.  The TY partial vectors are summed in
-// shared memory in lane order; when the columns are split into S > 1
-// chunks the chunk partials are summed in a fixed order by the block that
-// finishes a row tile last.
+// matching block of x (its micro-kernel).  For misaligned operands (scalar
+// loads) a warp item is TXW*V rows
+// (each lane owns V consecutive rows, one 16-byte pack per column: the m_r
+// of the micro-kernel) by a chunk of KC columns (n_c), walked by TYW =
+// 32/TXW column lanes, so one load instruction of the warp reads TYW column
+// segments of TXW*16 bytes.  The TYW partial vectors are summed by a fixed
+// butterfly of shuffles; when the columns are split into S > 1 chunks the
+// chunk partials are summed in a fixed order by the warp that finishes a row
+// item last.  Warps work on items independently (grid-stride over items).
 #include "gb_common.cuh"
 #include "gb_internal.h"
 
 namespace gb {
 namespace {
 
-template <typename T, int V, int TX, int U>
-__global__ void __launch_bounds__(kThreads)
+// Sum over the lanes that share lane % TXW (offsets 16, 8, ..., TXW), in a
+// fixed order; every lane ends with its group's total.
+template <int TXW>
+__device__ __forceinline__ double sum_over_ty(double v) {
+#pragma unroll
+  for (int o = 16; o >= TXW; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+template <int TXW>
+__device__ __forceinline__ float sum_over_ty_f(float v) {
+#pragma unroll
+  for (int o = 16; o >= TXW; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <typename T, int V, int TXW, int U, bool LONG>
+__global__ void __launch_bounds__(kThreads, 3)
     gemv_col_kernel(int64_t m, int64_t n, T alpha, const T* __restrict__ A, int64_t lda,
                     const T* __restrict__ x, T* __restrict__ c, const Split sp, int64_t KC,
-                    int64_t units) {
+                    int64_t items) {
+  constexpr int TYW = 32 / TXW;
+  constexpr int ROWS = TXW * V;  // rows per warp item
+  // LONG (FP32 only): a lane's chain would exceed 64 products per row, so its
+  // FP32 partial moves into FP64 every FLUSH bodies
+  constexpr int FLUSH = LONG ? (64 / U > 0 ? 64 / U : 1) : 1 << 30;
+
   const int S = sp.S;
-  constexpr int TY = kThreads / TX;
-  constexpr int RT = TX * V;  // rows per tile
-  constexpr int FLUSH = (sizeof(T) == 4) ? (64 / U > 0 ? 64 / U : 1) : 1 << 30;
+  const int lane = threadIdx.x & 31;
+  const int tx = lane % TXW;
+  const int ty = lane / TXW;
+  const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
 
-  __shared__ double red[kThreads * V];
-  __shared__ int flag;
-
-  const int tx = threadIdx.x % TX;
-  const int ty = threadIdx.x / TX;
-
-  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int64_t rt = u / S;
-    const int s = (int)(u - rt * S);
-    const int64_t i0 = rt * RT + (int64_t)tx * V;
+  for (int64_t it = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5; it < items; it += nwarps) {
+    const int64_t ri = it / S;
+    const int s = (int)(it - ri * S);
+    const int64_t rbase = ri * ROWS;
+    const int64_t i0 = rbase + (int64_t)tx * V;
     const int64_t k0 = (int64_t)s * KC;
     const int64_t k1 = (k0 + KC < n) ? k0 + KC : n;
     const bool full = i0 + V <= m;
-    const bool any = i0 < m;
-    const T* Ai = A + (any ? i0 : 0);
 
     T acc[V];
     double tot[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) { acc[v] = T(0); tot[v] = 0.0; }
 
-    auto load = [&](int64_t j) {
-      Pack<T, V> p;
-      if (full) {
-        p = ld_stream<T, V>(Ai + j * lda);
-      } else {
+    const int64_t cstep = (int64_t)TYW * lda;  // pointer step between a lane's columns
+    if (full) {
+      const T* pa = A + i0 + (k0 + ty) * lda;   // this lane's pack of column k0 + ty
+      const T* px = x + k0 + ty;
+      int64_t j = k0 + ty;
+      int body = 0;
+#pragma unroll 1
+      for (; j + (int64_t)(U - 1) * TYW < k1; j += (int64_t)U * TYW) {
+        Pack<T, V> ap[U];
+        T xs[U];
 #pragma unroll
-        for (int v = 0; v < V; ++v) p.v[v] = (i0 + v < m) ? __ldcs(Ai + v + j * lda) : T(0);
+        for (int q = 0; q < U; ++q) {
+          xs[q] = __ldg(px + q * TYW);
+          ap[q] = ld_stream<T, V>(pa + q * cstep);
+        }
+        pa += U * cstep;
+        px += U * TYW;
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc[v] = fma_rn(ap[q].v[v], xs[q], acc[v]);
+        if constexpr (LONG) {
+          if (++body == FLUSH) {
+            body = 0;
+#pragma unroll
+            for (int v = 0; v < V; ++v) { tot[v] = __dadd_rn(tot[v], (double)acc[v]); acc[v] = T(0); }
+          }
+        }
       }
-      return p;
-    };
+#pragma unroll 1
+      for (; j < k1; j += TYW, pa += cstep, px += TYW) {
+        const T xs = __ldg(px);
+        const Pack<T, V> ap = ld_stream<T, V>(pa);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = fma_rn(ap.v[v], xs, acc[v]);
+      }
+    } else if (i0 < m) {  // the rows of the last item stop inside this lane's pack
+      const T* pa = A + i0 + (k0 + ty) * lda;
+      int body = 0;
+      for (int64_t j = k0 + ty; j < k1; j += TYW, pa += cstep) {
+        const T xs = __ldg(x + j);
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          if (i0 + v < m) acc[v] = fma_rn(__ldcs(pa + v), xs, acc[v]);
+        if constexpr (LONG) {
+          if (++body == 64) {
+            body = 0;
+#pragma unroll
+            for (int v = 0; v < V; ++v) { tot[v] = __dadd_rn(tot[v], (double)acc[v]); acc[v] = T(0); }
+          }
+        }
+      }
+    }
 
-    int64_t j = k0 + ty;
-    int body = 0;
-    if (any) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      if constexpr (sizeof(T) == 4 && !LONG) tot[v] = (double)sum_over_ty_f<TXW>(acc[v]);
+      else tot[v] = sum_over_ty<TXW>(__dadd_rn(tot[v], (double)acc[v]));
+    }
+
+    if (S == 1) {
+      if (ty == 0) {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          if (i0 + v < m) c[i0 + v] = update_from(c[i0 + v], alpha, tot[v]);
+      }
+    } else {
+      if (ty == 0) {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          if (i0 + v < m) sp.part[(int64_t)s * m + i0 + v] = tot[v];
+      }
+      const int rows = (int)((m - rbase < ROWS) ? m - rbase : ROWS);
+      warp_split_finish<T>(sp, ri, s, rbase, rows, c, alpha);
+    }
+  }
+}
+
+// 16-byte aligned operands: block tiles.  A work unit is a tile of RT = TX*V
+// rows by a chunk of KC columns; thread (tx, ty) owns rows tx*V .. tx*V+V-1
+// of the tile (one 16-byte pack per column) and every TY-th column of the
+// chunk, with U packs in flight.  Block b takes the consecutive units
+// [b*units/G, (b+1)*units/G), so the blocks divide the work evenly and each
+// reads long runs of consecutive columns.  The TY partial vectors are summed
+// through shared memory in ty order; S > 1 chunk partials are combined by
+// block_split_finish.  FP32 sums stay in FP32 (chains of at most 64
+// products, then a compensated FP32 sum).
+template <typename T, int V, int TX, int U, bool LONG>
+__global__ void __launch_bounds__(kThreads, 4)
+    gemv_col_tile_kernel(int64_t m, int64_t n, T alpha, const T* __restrict__ A, int64_t lda,
+                         const T* __restrict__ x, T* __restrict__ c, const Split sp, int64_t KC,
+                         int64_t units) {
+  constexpr int TY = kThreads / TX;
+  constexpr int RT = TX * V;  // rows per tile
+  constexpr int FLUSH = LONG ? (64 / U > 0 ? 64 / U : 1) : 1 << 30;
+  __shared__ T redT[kThreads * V];
+  __shared__ double red_d[kThreads];
+  __shared__ int flag;
+
+  const int tx = threadIdx.x % TX;
+  const int ty = threadIdx.x / TX;
+  const int S = sp.S;
+  const int64_t u0 = units * blockIdx.x / gridDim.x;
+  const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
+  const int64_t cstep = (int64_t)TY * lda;  // between a thread's columns
+
+  for (int64_t u = u0; u < u1; ++u) {
+    const int64_t rt = u / S;
+    const int s = (int)(u - rt * S);
+    const int64_t i0 = rt * RT + (int64_t)tx * V;
+    const int64_t k0 = (int64_t)s * KC;
+    const int64_t k1 = (k0 + KC < n) ? k0 + KC : n;
+
+    T acc[V], hi[V], lo[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) { acc[v] = T(0); hi[v] = T(0); lo[v] = T(0); }
+
+    if (i0 + V <= m) {
+      const T* pa = A + i0 + (k0 + ty) * lda;
+      int64_t j = k0 + ty;
+      int body = 0;
+#pragma unroll 1
       for (; j + (int64_t)(U - 1) * TY < k1; j += (int64_t)U * TY) {
         Pack<T, V> ap[U];
         T xs[U];
 #pragma unroll
         for (int q = 0; q < U; ++q) {
+          ap[q] = ld_stream<T, V>(pa + q * cstep);
           xs[q] = __ldg(x + j + q * TY);
-          ap[q] = load(j + q * TY);
         }
+        pa += U * cstep;
 #pragma unroll
         for (int q = 0; q < U; ++q)
 #pragma unroll
           for (int v = 0; v < V; ++v) acc[v] = fma_rn(ap[q].v[v], xs[q], acc[v]);
-        if constexpr (sizeof(T) == 4) {
+        if constexpr (LONG) {
           if (++body == FLUSH) {
             body = 0;
 #pragma unroll
-            for (int v = 0; v < V; ++v) { tot[v] = __dadd_rn(tot[v], (double)acc[v]); acc[v] = 0.f; }
+            for (int v = 0; v < V; ++v) {
+              float e;
+              two_sum_f(hi[v], acc[v], hi[v], e);
+              lo[v] = __fadd_rn(lo[v], e);
+              acc[v] = T(0);
+            }
           }
         }
       }
-      for (; j < k1; j += TY) {
+#pragma unroll 1
+      for (; j < k1; j += TY, pa += cstep) {
+        const Pack<T, V> ap = ld_stream<T, V>(pa);
         const T xs = __ldg(x + j);
-        const Pack<T, V> ap = load(j);
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = fma_rn(ap.v[v], xs, acc[v]);
       }
-    }
+    } else if (i0 < m) {  // the last rows of the matrix stop inside this thread's pack
+      int body = 0;
+      for (int64_t j = k0 + ty; j < k1; j += TY) {
+        const T xs = __ldg(x + j);
 #pragma unroll
-    for (int v = 0; v < V; ++v) red[ty * RT + tx * V + v] = __dadd_rn(tot[v], (double)acc[v]);
-    __syncthreads();
-    for (int r = threadIdx.x; r < RT; r += kThreads) {
-      const int64_t row = rt * RT + r;
-      double t = 0.0;
-      for (int y = 0; y < TY; ++y) t = __dadd_rn(t, red[y * RT + r]);
-      if (row < m) {
-        if (S == 1) c[row] = update(c[row], alpha, t);
-        else sp.part[(int64_t)s * m + row] = t;
+        for (int v = 0; v < V; ++v)
+          if (i0 + v < m) acc[v] = fma_rn(__ldcs(A + i0 + v + j * lda), xs, acc[v]);
+        if constexpr (LONG) {
+          if (++body == 64) {
+            body = 0;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              float e;
+              two_sum_f(hi[v], acc[v], hi[v], e);
+              lo[v] = __fadd_rn(lo[v], e);
+              acc[v] = T(0);
+            }
+          }
+        }
       }
     }
+    if constexpr (LONG) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = hi[v] + (lo[v] + acc[v]);
+    }
+
+    __syncthreads();  // redT is free
+#pragma unroll
+    for (int v = 0; v < V; ++v) redT[ty * RT + tx * V + v] = acc[v];
     __syncthreads();
+    for (int r = threadIdx.x; r < RT; r += kThreads) {
+      T t = T(0);
+      for (int y = 0; y < TY; ++y) t = t + redT[y * RT + r];
+      const int64_t row = rt * RT + r;
+      if (row < m) {
+        if (S == 1) c[row] = update(c[row], alpha, t);
+        else sp.part[(int64_t)s * m + row] = (double)t;
+      }
+    }
     if (S > 1) {
       const int64_t t0 = rt * RT;
-      split_finish<T>(sp, rt, s, t0, (m - t0 < RT) ? m - t0 : RT, c, alpha, red, &flag);
+      block_split_finish<T>(sp, rt, s, t0, (m - t0 < RT) ? m - t0 : RT, c, alpha, red_d, &flag);
     }
   }
 }
 
-template <typename T, int V, int TX>
-int launch(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
-  auto kern = gemv_col_kernel<T, V, TX, 4>;
+template <typename T, int V, int TX, bool LONG>
+int launch_tile(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
+  auto kern = gemv_col_tile_kernel<T, V, TX, kColTileU, LONG>;
   const int grid = grid_size((const void*)kern, p.units);
   kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c, p.split, p.kc, p.units);
   return 0;
 }
 
-template <typename T, int V>
-int by_tx(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
-  switch (p.tx) {
-    case 64: return launch<T, V, 64>(a, p, st);
-    case 32: return launch<T, V, 32>(a, p, st);
-    case 16: return launch<T, V, 16>(a, p, st);
-    case 8: return launch<T, V, 8>(a, p, st);
-    case 4: return launch<T, V, 4>(a, p, st);
-    case 2: return launch<T, V, 2>(a, p, st);
-    default: return launch<T, V, 1>(a, p, st);
+template <typename T, int V, int TXW, bool LONG>
+int launch(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
+  auto kern = gemv_col_kernel<T, V, TXW, 8, LONG>;
+  const int64_t blocks = (p.units + kThreads / 32 - 1) / (kThreads / 32);
+  const int grid = grid_size((const void*)kern, blocks);
+  kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c, p.split, p.kc, p.units);
+  return 0;
+}
+
+template <typename T, int V, bool LONG>
+int by_txw(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
+  if constexpr (V > 1) {  // 16-byte aligned operands: block tiles (tx = threads along the rows)
+    switch (p.txw) {
+      case 64: return launch_tile<T, V, 64, LONG>(a, p, st);
+      case 32: return launch_tile<T, V, 32, LONG>(a, p, st);
+      case 16: return launch_tile<T, V, 16, LONG>(a, p, st);
+      case 8: return launch_tile<T, V, 8, LONG>(a, p, st);
+      case 4: return launch_tile<T, V, 4, LONG>(a, p, st);
+      case 2: return launch_tile<T, V, 2, LONG>(a, p, st);
+      default: return launch_tile<T, V, 1, LONG>(a, p, st);
+    }
+  } else {
+    switch (p.txw) {
+      case 32: return launch<T, V, 32, LONG>(a, p, st);
+      case 16: return launch<T, V, 16, LONG>(a, p, st);
+      case 8: return launch<T, V, 8, LONG>(a, p, st);
+      case 4: return launch<T, V, 4, LONG>(a, p, st);
+      case 2: return launch<T, V, 2, LONG>(a, p, st);
+      default: return launch<T, V, 1, LONG>(a, p, st);
+    }
   }
 }
 
@@ -132,8 +309,14 @@ int by_tx(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
 
 template <typename T>
 int gemv_col_launch(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
-  if (p.vec) return by_tx<T, 16 / sizeof(T)>(a, p, st);
-  return by_tx<T, 1>(a, p, st);
+  constexpr int V = 16 / sizeof(T);
+  if constexpr (sizeof(T) == 4) {
+    if (p.vec) return p.long_chain ? by_txw<T, V, true>(a, p, st) : by_txw<T, V, false>(a, p, st);
+    return p.long_chain ? by_txw<T, 1, true>(a, p, st) : by_txw<T, 1, false>(a, p, st);
+  } else {
+    if (p.vec) return by_txw<T, V, false>(a, p, st);
+    return by_txw<T, 1, false>(a, p, st);
+  }
 }
 
 template int gemv_col_launch<float>(const GemvArgs<float>&, const GemvPlan&, cudaStream_t);

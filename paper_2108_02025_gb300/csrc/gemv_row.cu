@@ -1,108 +1,224 @@
 // Row-major GEMV, c_i <- c_i + alpha * sum_j A[i*lda + j] x_j.
 //
 // Alg. 2 of the paper (Sec. 4.2) hands each row, a unit-stride dot product,
-// to one worker; Loop-1 (rows) is the parallel loop.  Here a row goes to a
-// group of LPR lanes of a warp (LPR = 32 for long rows, fewer for short ones)
-// that streams it with 16-byte loads; each group carries RW rows at once so
-// that every x pack it loads serves RW rows and each lane has RW*U loads of
-// A in flight.  When there are too few rows to fill the GPU, the columns are
-// split into S chunks (the Alg. 4 idea of blocking the index range) and the
-// chunk partials are summed in a fixed order by the block that finishes a
-// row tile last.
+// to one worker; Loop-1 (rows) is the parallel loop.  On the GPU the rows
+// are streamed so that every block reads one contiguous stretch of memory:
+//
+// * long rows (more than 256 16-byte packs): a work unit is one chunk of KC
+//   columns of one row (KC = n unless the rows are too few to fill the GPU,
+//   when the columns are split into S chunks, the blocking of the index
+//   range of Alg. 4).  Block b takes the consecutive units
+//   [b*units/G, (b+1)*units/G) and streams each with all 256 threads
+//   (16-byte loads, U packs per thread in flight), then sums the unit in a
+//   fixed order (warp butterfly, then warps in order).  A split row's chunk
+//   partials are summed in chunk order by the block that finishes the row.
+// * short rows (at most 256 packs): LPR lanes share a row, each holding up to
+//   8 of its packs, so a block iteration reads 256/LPR consecutive rows; the
+//   LPR lanes of a row are summed by a butterfly.
+// * FP32 rows are summed in FP32 throughout (chains of at most 64 products,
+//   then a compensated FP32 sum); split partials are combined in FP64.
+// * misaligned operands (no 16-byte packs): warp items of RW rows with
+//   scalar loads.
 #include "gb_common.cuh"
 #include "gb_internal.h"
 
 namespace gb {
 namespace {
 
-template <typename T, int V, int LPR, int RW, int U>
-__global__ void __launch_bounds__(kThreads)
-    gemv_row_kernel(int64_t m, int64_t n, T alpha, const T* __restrict__ A, int64_t lda,
-                    const T* __restrict__ x, T* __restrict__ c, const Split sp, int64_t KC,
-                    int64_t units) {
-  const int S = sp.S;
-  constexpr int GPW = 32 / LPR;                   // row groups per warp
-  constexpr int GROUPS = kThreads / LPR;          // row groups per block
-  constexpr int ROWS = GROUPS * RW;               // rows per block tile
-  constexpr int64_t STEP = (int64_t)LPR * V;      // columns a group covers per pack
-  // FP32 partial sums move into FP64 after at most 64 terms per lane
-  constexpr int FLUSH = (sizeof(T) == 4) ? (64 / (U * V) > 0 ? 64 / (U * V) : 1) : 1 << 30;
+// Sum of one value per thread over the block in a fixed order (warp
+// butterfly, then the 8 warp totals in order), in the element type;
+// the result is valid in thread 0.  Synchronises the block.
+template <typename T>
+__device__ __forceinline__ T block_total(T v, T* red) {
+  if constexpr (sizeof(T) == 4) v = group_sum_f<32>(v);
+  else v = group_sum<32>(v);
+  __syncthreads();  // red is free (its previous use has been read)
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T t = T(0);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < kThreads / 32; ++k) t = t + red[k];
+  }
+  return t;
+}
 
-  __shared__ double red[kThreads];
+// Long rows.  unit u = (row u / S, chunk u % S).
+template <typename T, int V, int U, bool LONG>
+__global__ void __launch_bounds__(kThreads, 4)
+    gemv_row_long_kernel(int64_t m, int64_t n, T alpha, const T* __restrict__ A, int64_t lda,
+                         const T* __restrict__ x, T* __restrict__ c, const Split sp, int64_t KC,
+                         int64_t units) {
+  constexpr int64_t STEP = (int64_t)kThreads * V;  // columns the block covers per pack
+  // LONG (FP32 only): a thread's chain would exceed 64 products, so every
+  // FLUSH bodies it is folded into a compensated FP32 sum (TwoSum)
+  constexpr int FLUSH = LONG ? (64 / (U * V) > 0 ? 64 / (U * V) : 1) : 1 << 30;
+  __shared__ double red_d[kThreads / 32];
   __shared__ int flag;
+  T* red = reinterpret_cast<T*>(red_d);
 
-  const int lane = threadIdx.x & 31;
-  const int l = lane % LPR;
-  const int grp = (threadIdx.x >> 5) * GPW + lane / LPR;
-
-  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int64_t rt = u / S;
-    const int s = (int)(u - rt * S);
-    const int64_t row0 = rt * ROWS + (int64_t)grp * RW;
+  const int S = sp.S;
+  const int64_t u0 = units * blockIdx.x / gridDim.x;
+  const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
+  for (int64_t u = u0; u < u1; ++u) {
+    const int64_t row = u / S;
+    const int s = (int)(u - row * S);
     const int64_t k0 = (int64_t)s * KC;
     const int64_t k1 = (k0 + KC < n) ? k0 + KC : n;
-    const int64_t kv1 = k0 + ((k1 - k0) / V) * V;  // end of whole packs
+    const int64_t kv1 = k0 + ((k1 - k0) / V) * V;
+    const T* Ar = A + row * lda;
 
-    const T* Ar[RW];
-#pragma unroll
-    for (int r = 0; r < RW; ++r) {
-      const int64_t row = (row0 + r < m) ? row0 + r : m - 1;  // clamp: the tail tile re-reads a row
-      Ar[r] = A + row * lda;
-    }
-
-    double tot[RW];
-    T acc[RW];
-#pragma unroll
-    for (int r = 0; r < RW; ++r) { tot[r] = 0.0; acc[r] = T(0); }
-
-    int64_t j = k0 + (int64_t)l * V;
+    T acc = T(0), hi = T(0), lo = T(0);
     int body = 0;
+    int64_t j = k0 + (int64_t)threadIdx.x * V;
+#pragma unroll 1
     for (; j + (U - 1) * STEP < kv1; j += U * STEP) {
-      Pack<T, V> xp[U];
-      Pack<T, V> ap[U][RW];
+      Pack<T, V> ap[U], xp[U];
 #pragma unroll
       for (int q = 0; q < U; ++q) {
+        ap[q] = ld_stream<T, V>(Ar + j + q * STEP);
         xp[q] = ld_keep<T, V>(x + j + q * STEP);
-#pragma unroll
-        for (int r = 0; r < RW; ++r) ap[q][r] = ld_stream<T, V>(Ar[r] + j + q * STEP);
       }
 #pragma unroll
       for (int q = 0; q < U; ++q)
 #pragma unroll
-        for (int r = 0; r < RW; ++r)
-#pragma unroll
-          for (int v = 0; v < V; ++v) acc[r] = fma_rn(ap[q][r].v[v], xp[q].v[v], acc[r]);
-      if constexpr (sizeof(T) == 4) {
+        for (int v = 0; v < V; ++v) acc = fma_rn(ap[q].v[v], xp[q].v[v], acc);
+      if constexpr (LONG) {
         if (++body == FLUSH) {
           body = 0;
-#pragma unroll
-          for (int r = 0; r < RW; ++r) { tot[r] = __dadd_rn(tot[r], (double)acc[r]); acc[r] = 0.f; }
+          float e;
+          two_sum_f(hi, acc, hi, e);
+          lo = __fadd_rn(lo, e);
+          acc = T(0);
         }
       }
     }
-    for (; j < kv1; j += STEP) {  // remaining whole packs
-      const Pack<T, V> xq = ld_keep<T, V>(x + j);
+#pragma unroll 1
+    for (; j < kv1; j += STEP) {
+      const Pack<T, V> ap = ld_stream<T, V>(Ar + j), xp = ld_keep<T, V>(x + j);
 #pragma unroll
-      for (int r = 0; r < RW; ++r) {
-        const Pack<T, V> aq = ld_stream<T, V>(Ar[r] + j);
-#pragma unroll
-        for (int v = 0; v < V; ++v) acc[r] = fma_rn(aq.v[v], xq.v[v], acc[r]);
+      for (int v = 0; v < V; ++v) acc = fma_rn(ap.v[v], xp.v[v], acc);
+    }
+    if (kv1 + threadIdx.x < k1) {  // ragged end (< V columns)
+      const int64_t jj = kv1 + threadIdx.x;
+      acc = fma_rn(__ldcs(Ar + jj), __ldg(x + jj), acc);
+    }
+    if constexpr (LONG) acc = hi + (lo + acc);
+
+    const T total = block_total<T>(acc, red);
+    if (S == 1) {
+      if (threadIdx.x == 0) c[row] = update(c[row], alpha, total);
+    } else {
+      if (threadIdx.x == 0) sp.part[(int64_t)s * m + row] = (double)total;
+      if (arrive_last(sp.tickets + row, (unsigned)S, &flag)) {
+        // the row's S chunk partials in FP64: thread t adds chunks t, t+256,
+        // ... in order, then the fixed block order
+        double p = 0.0;
+        for (int q = threadIdx.x; q < S; q += kThreads) p = __dadd_rn(p, __ldcg(sp.part + (int64_t)q * m + row));
+        const double sum = block_total<double>(p, red_d);
+        if (threadIdx.x == 0) {
+          c[row] = update_from(c[row], alpha, sum);
+          sp.tickets[row] = 0u;
+        }
       }
     }
-    for (int64_t jj = kv1 + l; jj < k1; jj += LPR) {  // ragged end of the row (< V columns)
-      const T xs = __ldg(x + jj);
-#pragma unroll
-      for (int r = 0; r < RW; ++r) acc[r] = fma_rn(__ldcs(Ar[r] + jj), xs, acc[r]);
-    }
+  }
+}
 
+// Short rows (S = 1, at most 32*8 packs).  LPR lanes per row, each with up
+// to 8 packs (pack k*LPR + l of the row), so a block iteration reads
+// 256/LPR consecutive rows; block b takes rows [b*m/G, (b+1)*m/G).
+template <typename T, int V, int LPR>
+__global__ void __launch_bounds__(kThreads, 4)
+    gemv_row_short_kernel(int64_t m, int64_t n, T alpha, const T* __restrict__ A, int64_t lda,
+                          const T* __restrict__ x, T* __restrict__ c) {
+  constexpr int GROUPS = kThreads / LPR;  // rows per block iteration
+  constexpr int PMAX = 8;
+  const int l = threadIdx.x % LPR;
+  const int g = threadIdx.x / LPR;
+  const int64_t r0 = m * blockIdx.x / gridDim.x;
+  const int64_t r1 = m * (blockIdx.x + 1) / gridDim.x;
+  const int64_t packs = n / V;
+  const int64_t kv1 = packs * V;
+  const bool tail = kv1 + l < n;  // ragged end: lane l takes column kv1 + l
+  const T xt = tail ? __ldg(x + kv1 + l) : T(0);
+
+  // every thread runs the same number of iterations (the butterfly needs
+  // whole warps); rows past r1 are predicated off
+#pragma unroll 1
+  for (int64_t base = r0; base < r1; base += GROUPS) {
+    const int64_t row = base + g;
+    const bool ok = row < r1;
+    const T* Ar = A + (ok ? row : r0) * lda;
+    Pack<T, V> ap[PMAX];
+#pragma unroll
+    for (int k = 0; k < PMAX; ++k) {
+      const int64_t p = (int64_t)k * LPR + l;
+      if (ok && p < packs) ap[k] = ld_stream<T, V>(Ar + p * V);
+    }
+    T acc = (ok && tail) ? __ldcs(Ar + kv1 + l) * xt : T(0);
+#pragma unroll
+    for (int k = 0; k < PMAX; ++k) {
+      const int64_t p = (int64_t)k * LPR + l;
+      if (ok && p < packs) {
+        const Pack<T, V> xp = ld_keep<T, V>(x + p * V);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc = fma_rn(ap[k].v[v], xp.v[v], acc);
+      }
+    }
+    T sum;
+    if constexpr (sizeof(T) == 4) sum = group_sum_f<LPR>(acc);
+    else sum = group_sum<LPR>(acc);
+    if (ok && l == 0) c[row] = update(c[row], alpha, sum);
+  }
+}
+
+// Misaligned operands: warp items of RW rows (GPW = 32/LPR groups of RW rows)
+// over chunks of KC columns, scalar loads.
+template <typename T, int LPR, int RW>
+__global__ void __launch_bounds__(kThreads, 4)
+    gemv_row_scalar_kernel(int64_t m, int64_t n, T alpha, const T* __restrict__ A, int64_t lda,
+                           const T* __restrict__ x, T* __restrict__ c, const Split sp, int64_t KC,
+                           int64_t items) {
+  constexpr int GPW = 32 / LPR;
+  constexpr int ROWS = GPW * RW;
+  const int S = sp.S;
+  const int lane = threadIdx.x & 31;
+  const int l = lane % LPR;
+  const int grp = lane / LPR;
+  const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
+  for (int64_t it = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5; it < items; it += nwarps) {
+    const int64_t ri = it / S;
+    const int s = (int)(it - ri * S);
+    const int64_t rbase = ri * ROWS;
+    const int64_t row0 = rbase + (int64_t)grp * RW;
+    const int64_t k0 = (int64_t)s * KC;
+    const int64_t k1 = (k0 + KC < n) ? k0 + KC : n;
+    double tot[RW];
+    T acc[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) { tot[r] = 0.0; acc[r] = T(0); }
+    int cnt = 0;
+    for (int64_t j = k0 + l; j < k1; j += LPR) {
+      const T xs = __ldg(x + j);
+#pragma unroll
+      for (int r = 0; r < RW; ++r) {
+        const int64_t row = (row0 + r < m) ? row0 + r : m - 1;
+        acc[r] = fma_rn(__ldcs(A + row * lda + j), xs, acc[r]);
+      }
+      if (++cnt == 64) {  // chains move into FP64 after 64 products
+        cnt = 0;
+#pragma unroll
+        for (int r = 0; r < RW; ++r) { tot[r] = __dadd_rn(tot[r], (double)acc[r]); acc[r] = T(0); }
+      }
+    }
 #pragma unroll
     for (int r = 0; r < RW; ++r) tot[r] = group_sum<LPR>(__dadd_rn(tot[r], (double)acc[r]));
-
     if (S == 1) {
       if (l == 0) {
 #pragma unroll
         for (int r = 0; r < RW; ++r)
-          if (row0 + r < m) c[row0 + r] = update(c[row0 + r], alpha, tot[r]);
+          if (row0 + r < m) c[row0 + r] = update_from(c[row0 + r], alpha, tot[r]);
       }
     } else {
       if (l == 0) {
@@ -110,30 +226,36 @@ __global__ void __launch_bounds__(kThreads)
         for (int r = 0; r < RW; ++r)
           if (row0 + r < m) sp.part[(int64_t)s * m + row0 + r] = tot[r];
       }
-      const int64_t t0 = rt * ROWS;
-      split_finish<T>(sp, rt, s, t0, (m - t0 < ROWS) ? m - t0 : ROWS, c, alpha, red, &flag);
+      const int rows = (int)((m - rbase < ROWS) ? m - rbase : ROWS);
+      warp_split_finish<T>(sp, ri, s, rbase, rows, c, alpha);
     }
   }
 }
 
-template <typename T, int V, int LPR, int RW, int U>
-int launch(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
-  auto kern = gemv_row_kernel<T, V, LPR, RW, U>;
+template <typename T, int V, bool LONG>
+int launch_long(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
+  auto kern = gemv_row_long_kernel<T, V, kRowLongU, LONG>;
   const int grid = grid_size((const void*)kern, p.units);
   kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c, p.split, p.kc, p.units);
   return 0;
 }
 
-template <typename T, int V, int RW, int U>
-int by_lpr(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
-  switch (p.lpr) {
-    case 32: return launch<T, V, 32, RW, U>(a, p, st);
-    case 16: return launch<T, V, 16, RW, U>(a, p, st);
-    case 8: return launch<T, V, 8, RW, U>(a, p, st);
-    case 4: return launch<T, V, 4, RW, U>(a, p, st);
-    case 2: return launch<T, V, 2, RW, U>(a, p, st);
-    default: return launch<T, V, 1, RW, U>(a, p, st);
-  }
+template <typename T, int V, int LPR>
+int launch_short(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
+  auto kern = gemv_row_short_kernel<T, V, LPR>;
+  constexpr int64_t rows_per_iter = kThreads / LPR;
+  const int grid = grid_size((const void*)kern, (a.m + rows_per_iter - 1) / rows_per_iter);
+  kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c);
+  return 0;
+}
+
+template <typename T, int LPR>
+int launch_scalar(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
+  auto kern = gemv_row_scalar_kernel<T, LPR, kRowScalarRW>;
+  const int64_t blocks = (p.units + kThreads / 32 - 1) / (kThreads / 32);
+  const int grid = grid_size((const void*)kern, blocks);
+  kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c, p.split, p.kc, p.units);
+  return 0;
 }
 
 }  // namespace
@@ -141,12 +263,30 @@ int by_lpr(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
 template <typename T>
 int gemv_row_launch(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
   constexpr int V = 16 / sizeof(T);
-  if (p.vec) {
-    if (p.rw == 8) return by_lpr<T, V, 8, 2>(a, p, st);
-    return by_lpr<T, V, 4, 2>(a, p, st);
+  if (p.kind == GemvPlan::kRowLong) {
+    if constexpr (sizeof(T) == 4)
+      return p.long_chain ? launch_long<T, V, true>(a, p, st) : launch_long<T, V, false>(a, p, st);
+    else
+      return launch_long<T, V, false>(a, p, st);
   }
-  if (p.rw == 8) return by_lpr<T, 1, 8, 2>(a, p, st);
-  return by_lpr<T, 1, 4, 2>(a, p, st);
+  if (p.kind == GemvPlan::kRowShort) {
+    switch (p.lpr) {
+      case 32: return launch_short<T, V, 32>(a, p, st);
+      case 16: return launch_short<T, V, 16>(a, p, st);
+      case 8: return launch_short<T, V, 8>(a, p, st);
+      case 4: return launch_short<T, V, 4>(a, p, st);
+      case 2: return launch_short<T, V, 2>(a, p, st);
+      default: return launch_short<T, V, 1>(a, p, st);
+    }
+  }
+  switch (p.lpr) {
+    case 32: return launch_scalar<T, 32>(a, p, st);
+    case 16: return launch_scalar<T, 16>(a, p, st);
+    case 8: return launch_scalar<T, 8>(a, p, st);
+    case 4: return launch_scalar<T, 4>(a, p, st);
+    case 2: return launch_scalar<T, 2>(a, p, st);
+    default: return launch_scalar<T, 1>(a, p, st);
+  }
 }
 
 template int gemv_row_launch<float>(const GemvArgs<float>&, const GemvPlan&, cudaStream_t);

@@ -101,7 +101,7 @@ def test_ger_validation(f):
 def test_workspace_bytes():
     wb = gb.gb_workspace_bytes
     assert wb(gb.OP_GER, gb.F64, 0, 1000, 1000) == 0
-    assert wb(gb.OP_GEMV, gb.F64, 0, 16384, 16384) == 0               # enough rows: no split
+    assert wb(gb.OP_GEMV, gb.F64, 0, 1048576, 64) == 0                # many rows: no split
     assert wb(gb.OP_GEMV, gb.F32, 0, 64, 1 << 20) > 0                 # wide: split sum
     assert wb(gb.OP_GEMV, gb.F32, 1, 64, 1 << 20) > 0
     assert wb(gb.OP_DOT, gb.F64, 0, 0, 1000) == 0                     # small DOT: one block
