@@ -6,7 +6,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "../../include/gbblas.h"
+#include "gbblas.h"
 #include "gb_internal.h"
 
 namespace gb {
@@ -178,7 +178,7 @@ inline RowShape row_shape(size_t e, bool vec, int64_t m, int64_t n) {
   if (vec) {  // long rows: blocks stream (row, chunk) units; one counter per row
     r.kind = GemvPlan::kRowLong;
     const int64_t quantum = 256 * V;
-    SplitShape s = block_split(m, n, quantum * kRowLongU, quantum, e);
+    SplitShape s = block_split(m, n, quantum * kRowLongU * (e == 8 ? 2 : 1), quantum, e);
     s.G = s.S;   // the long-row kernel sums a row's S partials in one level
     s.NG = 1;
     r.sp = s;

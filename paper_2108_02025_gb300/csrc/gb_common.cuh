@@ -102,6 +102,60 @@ __device__ __forceinline__ double fma_rn(double a, double b, double c) { return 
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
+// ---- FP64 products on the FP32 pipe --------------------------------------
+// GB300 issues FP64 FMAs at about 2 per clock per SM, too few for an FP64
+// GEMV to keep up with HBM.  The FP64 GEMV kernels therefore form part of
+// their products a*x with FP32 instructions: each operand is cut into a
+// 24-bit head and the next 23 bits (emu_split, integer operations on the
+// bit pattern, exact), the head product is formed exactly with an FMA
+// (TwoProduct), the two cross terms are added in FP32, and the running sum
+// is an unevaluated FP32 pair (H, L) updated with Knuth's TwoSum.  Dropped
+// parts are below 2^-45 of |a*x| per product; the pair is folded into the
+// FP64 sum every 32 products or fewer.  Operands outside 2^-30 <= |v| < 2^31 (zero,
+// subnormal, huge, Inf, NaN) take the FP64 FMA instead (emu_ok).
+
+__device__ __forceinline__ bool emu_ok(double v) {
+  const unsigned e = ((unsigned)__double2hiint(v) >> 20) & 0x7FFu;
+  return e - 993u <= 60u;  // biased exponent in [993, 1053]
+}
+
+// v == hi + lo + r with |r| < 2^-46 |v|: hi = v truncated to 24 significant
+// bits, lo = the next 23 bits.  Requires emu_ok(v).
+__device__ __forceinline__ void emu_split(double v, float& hi, float& lo) {
+  const unsigned h = (unsigned)__double2hiint(v), l = (unsigned)__double2loint(v);
+  const unsigned sgn = h & 0x80000000u;
+  const unsigned f = __funnelshift_l(l, h - (896u << 20), 3);  // rebias 1023 -> 127, shift into place
+  hi = __uint_as_float((f & 0x7FFFFFFFu) | sgn);
+  const unsigned ge = (f & 0x7F800000u) - (23u << 23);         // exponent 23 below hi's
+  lo = __fsub_rn(__uint_as_float(sgn | ge | ((l >> 6) & 0x7FFFFFu)), __uint_as_float(sgn | ge));
+}
+
+// (H, L) += a*x with FP32 instructions only; requires emu_ok(a) && emu_ok(x).
+__device__ __forceinline__ void emu_fma(float ah, float al, float xh, float xl, float& H, float& L) {
+  const float p = __fmul_rn(ah, xh);
+  const float e = __fmaf_rn(ah, xh, -p);              // ah*xh == p + e exactly
+  const float t = __fmaf_rn(ah, xl, __fmaf_rn(al, xh, e));
+  const float s = __fadd_rn(H, p);                    // TwoSum(H, p)
+  const float z = __fsub_rn(s, H);
+  const float err = __fadd_rn(__fsub_rn(H, __fsub_rn(s, z)), __fsub_rn(p, z));
+  H = s;
+  L = __fadd_rn(L, __fadd_rn(err, t));
+}
+
+// The FP64 fallback of a group of emulated packs (an operand out of range):
+// kept out of line, so that the hot path holds no FP64 instruction even when
+// the compiler predicates the branch around the call.
+template <int NP>
+struct DPacks {
+  double a[NP], x[NP];
+};
+template <int NP>
+__device__ __noinline__ double dfma_fallback(const DPacks<NP> p, double acc) {
+#pragma unroll
+  for (int k = 0; k < NP; ++k) acc = __fma_rn(p.a[k], p.x[k], acc);
+  return acc;
+}
+
 // Sum over aligned groups of W lanes with an xor butterfly: every lane of a
 // group ends with the same, order-fixed total.
 template <int W>

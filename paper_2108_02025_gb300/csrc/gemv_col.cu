@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(kThreads, 4)
   constexpr int TY = kThreads / TX;
   constexpr int RT = TX * V;  // rows per tile
   constexpr int FLUSH = LONG ? (64 / U > 0 ? 64 / U : 1) : 1 << 30;
+  constexpr int EFLUSH = 32 / (U - U / 2) > 0 ? 32 / (U - U / 2) : 1;
   __shared__ T redT[kThreads * V];
   __shared__ double red_d[kThreads];
   __shared__ int flag;
@@ -177,8 +178,10 @@ __global__ void __launch_bounds__(kThreads, 4)
     const int64_t k1 = (k0 + KC < n) ? k0 + KC : n;
 
     T acc[V], hi[V], lo[V];
+    float eh[V], el[V];  // FP64: pairs of the FP32-emulated products
 #pragma unroll
-    for (int v = 0; v < V; ++v) { acc[v] = T(0); hi[v] = T(0); lo[v] = T(0); }
+    for (int v = 0; v < V; ++v) { acc[v] = T(0); hi[v] = T(0); lo[v] = T(0); eh[v] = 0.f; el[v] = 0.f; }
+    int ebody = 0;
 
     if (i0 + V <= m) {
       const T* pa = A + i0 + (k0 + ty) * lda;
@@ -194,10 +197,63 @@ __global__ void __launch_bounds__(kThreads, 4)
           xs[q] = __ldg(x + j + q * TY);
         }
         pa += U * cstep;
+        if constexpr (sizeof(T) == 8) {
+          // FP64: the first half of the columns on the FP64 pipe, the second
+          // half with FP32 instructions (emu_fma) into the pairs (eh, el)
 #pragma unroll
-        for (int q = 0; q < U; ++q)
+          for (int q = 0; q < U / 2; ++q)
 #pragma unroll
-          for (int v = 0; v < V; ++v) acc[v] = fma_rn(ap[q].v[v], xs[q], acc[v]);
+            for (int v = 0; v < V; ++v) acc[v] = fma_rn(ap[q].v[v], xs[q], acc[v]);
+          bool ok = true;
+#pragma unroll
+          for (int q = U / 2; q < U; ++q) {
+            ok = ok && emu_ok(xs[q]);
+#pragma unroll
+            for (int v = 0; v < V; ++v) ok = ok && emu_ok(ap[q].v[v]);
+          }
+          // the choice is made for all the lanes that run here together (the
+          // active mask: lanes of one warp may leave this loop at different
+          // trips), so that the emulated path holds no FP64 instruction (a
+          // predicated-off one would still occupy the FP64 pipe)
+          if (__all_sync(__activemask(), ok)) {
+#pragma unroll
+            for (int q = U / 2; q < U; ++q) {
+              float xh, xl;
+              emu_split(xs[q], xh, xl);
+#pragma unroll
+              for (int v = 0; v < V; ++v) {
+                float ah, al;
+                emu_split(ap[q].v[v], ah, al);
+                emu_fma(ah, al, xh, xl, eh[v], el[v]);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              DPacks<U - U / 2> dp;
+#pragma unroll
+              for (int q = U / 2; q < U; ++q) {
+                dp.a[q - U / 2] = ap[q].v[v];
+                dp.x[q - U / 2] = xs[q];
+              }
+              acc[v] = dfma_fallback(dp, acc[v]);
+            }
+          }
+          if (++ebody == EFLUSH) {  // at most 32 products per row in the FP32 pairs
+            ebody = 0;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              acc[v] = __dadd_rn(acc[v], __dadd_rn((double)eh[v], (double)el[v]));
+              eh[v] = 0.f;
+              el[v] = 0.f;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < U; ++q)
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = fma_rn(ap[q].v[v], xs[q], acc[v]);
+        }
         if constexpr (LONG) {
           if (++body == FLUSH) {
             body = 0;
@@ -242,6 +298,10 @@ __global__ void __launch_bounds__(kThreads, 4)
     if constexpr (LONG) {
 #pragma unroll
       for (int v = 0; v < V; ++v) acc[v] = hi[v] + (lo[v] + acc[v]);
+    }
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = __dadd_rn(acc[v], __dadd_rn((double)eh[v], (double)el[v]));
     }
 
     __syncthreads();  // redT is free

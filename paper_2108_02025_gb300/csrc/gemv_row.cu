@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(kThreads, 4)
   // LONG (FP32 only): a thread's chain would exceed 64 products, so every
   // FLUSH bodies it is folded into a compensated FP32 sum (TwoSum)
   constexpr int FLUSH = LONG ? (64 / (U * V) > 0 ? 64 / (U * V) : 1) : 1 << 30;
+  constexpr int EFLUSH = 32 / ((U - U / 2) * V) > 0 ? 32 / ((U - U / 2) * V) : 1;
   __shared__ double red_d[kThreads / 32];
   __shared__ int flag;
   T* red = reinterpret_cast<T*>(red_d);
@@ -68,28 +69,78 @@ __global__ void __launch_bounds__(kThreads, 4)
     const int64_t kv1 = k0 + ((k1 - k0) / V) * V;
     const T* Ar = A + row * lda;
 
-    T acc = T(0), hi = T(0), lo = T(0);
+    T acc = T(0), acc2 = T(0), hi = T(0), lo = T(0);
+    float eh = 0.f, el = 0.f;  // FP64: the pair of the FP32-emulated products
     int body = 0;
     int64_t j = k0 + (int64_t)threadIdx.x * V;
+    // the main loop runs while the warp's last lane has U whole packs left,
+    // so that all 32 lanes take the same number of trips
+    const int64_t jlast = (int64_t)(31 - (threadIdx.x & 31)) * V;
 #pragma unroll 1
-    for (; j + (U - 1) * STEP < kv1; j += U * STEP) {
+    for (; j + jlast + (U - 1) * STEP < kv1; j += U * STEP) {
       Pack<T, V> ap[U], xp[U];
 #pragma unroll
-      for (int q = 0; q < U; ++q) {
-        ap[q] = ld_stream<T, V>(Ar + j + q * STEP);
-        xp[q] = ld_keep<T, V>(x + j + q * STEP);
-      }
+      for (int q = 0; q < U; ++q) ap[q] = ld_stream<T, V>(Ar + j + q * STEP);
 #pragma unroll
-      for (int q = 0; q < U; ++q)
+      for (int q = 0; q < U; ++q) xp[q] = ld_keep<T, V>(x + j + q * STEP);
+      if constexpr (sizeof(T) == 8) {
+        // FP64: the first half of the packs on the FP64 pipe, the second
+        // half with FP32 instructions (emu_fma) into the pair (eh, el).  The
+        // choice is made for all the lanes running here together (the active
+        // mask), so that the emulated path holds no FP64 instruction (a
+        // predicated-off one would still occupy the FP64 pipe).
 #pragma unroll
-        for (int v = 0; v < V; ++v) acc = fma_rn(ap[q].v[v], xp[q].v[v], acc);
-      if constexpr (LONG) {
-        if (++body == FLUSH) {
+        for (int q = 0; q < U / 2; ++q)
+#pragma unroll
+          for (int v = 0; v < V; ++v) {  // two FP64 chains (v), half the dependent latency
+            if (v == 0) acc = fma_rn(ap[q].v[v], xp[q].v[v], acc);
+            else acc2 = fma_rn(ap[q].v[v], xp[q].v[v], acc2);
+          }
+        bool ok = true;
+#pragma unroll
+        for (int q = U / 2; q < U; ++q)
+#pragma unroll
+          for (int v = 0; v < V; ++v) ok = ok && emu_ok(ap[q].v[v]) && emu_ok(xp[q].v[v]);
+        if (__all_sync(__activemask(), ok)) {
+#pragma unroll
+          for (int q = U / 2; q < U; ++q)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              float ah, al, xh, xl;
+              emu_split(ap[q].v[v], ah, al);
+              emu_split(xp[q].v[v], xh, xl);
+              emu_fma(ah, al, xh, xl, eh, el);
+            }
+        } else {
+          DPacks<(U - U / 2) * V> dp;
+#pragma unroll
+          for (int q = U / 2; q < U; ++q)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              dp.a[(q - U / 2) * V + v] = ap[q].v[v];
+              dp.x[(q - U / 2) * V + v] = xp[q].v[v];
+            }
+          acc = dfma_fallback(dp, acc);
+        }
+        if (++body == EFLUSH) {  // at most 32 products in the FP32 pair
           body = 0;
-          float e;
-          two_sum_f(hi, acc, hi, e);
-          lo = __fadd_rn(lo, e);
-          acc = T(0);
+          acc = __dadd_rn(acc, __dadd_rn((double)eh, (double)el));
+          eh = 0.f;
+          el = 0.f;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc = fma_rn(ap[q].v[v], xp[q].v[v], acc);
+        if constexpr (LONG) {
+          if (++body == FLUSH) {
+            body = 0;
+            float e;
+            two_sum_f(hi, acc, hi, e);
+            lo = __fadd_rn(lo, e);
+            acc = T(0);
+          }
         }
       }
     }
@@ -104,6 +155,10 @@ __global__ void __launch_bounds__(kThreads, 4)
       acc = fma_rn(__ldcs(Ar + jj), __ldg(x + jj), acc);
     }
     if constexpr (LONG) acc = hi + (lo + acc);
+    if constexpr (sizeof(T) == 8) {
+      acc = __dadd_rn(acc, acc2);
+      acc = __dadd_rn(acc, __dadd_rn((double)eh, (double)el));
+    }
 
     const T total = block_total<T>(acc, red);
     if (S == 1) {
@@ -129,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 4)
 // to 8 packs (pack k*LPR + l of the row), so a block iteration reads
 // 256/LPR consecutive rows; block b takes rows [b*m/G, (b+1)*m/G).
 template <typename T, int V, int LPR>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? 3 : 4)
     gemv_row_short_kernel(int64_t m, int64_t n, T alpha, const T* __restrict__ A, int64_t lda,
                           const T* __restrict__ x, T* __restrict__ c) {
   constexpr int GROUPS = kThreads / LPR;  // rows per block iteration
@@ -157,13 +212,69 @@ __global__ void __launch_bounds__(kThreads, 4)
       if (ok && p < packs) ap[k] = ld_stream<T, V>(Ar + p * V);
     }
     T acc = (ok && tail) ? __ldcs(Ar + kv1 + l) * xt : T(0);
+    if constexpr (sizeof(T) == 8) {
+      // FP64: packs 0..3 on the FP64 pipe, packs 4..7 with FP32 instructions
+      // (emu_fma) when every lane of the warp has all of them in range; the
+      // choice is made for the whole warp, so that the emulated path holds no
+      // FP64 instruction.
 #pragma unroll
-    for (int k = 0; k < PMAX; ++k) {
-      const int64_t p = (int64_t)k * LPR + l;
-      if (ok && p < packs) {
-        const Pack<T, V> xp = ld_keep<T, V>(x + p * V);
+      for (int k = 0; k < PMAX / 2; ++k) {
+        const int64_t p = (int64_t)k * LPR + l;
+        if (ok && p < packs) {
+          const Pack<T, V> xp = ld_keep<T, V>(x + p * V);
 #pragma unroll
-        for (int v = 0; v < V; ++v) acc = fma_rn(ap[k].v[v], xp.v[v], acc);
+          for (int v = 0; v < V; ++v) acc = fma_rn(ap[k].v[v], xp.v[v], acc);
+        }
+      }
+      Pack<T, V> xq[PMAX / 2];
+      bool good = true;
+#pragma unroll
+      for (int k = PMAX / 2; k < PMAX; ++k) {
+        const int64_t p = (int64_t)k * LPR + l;
+        const bool present = ok && p < packs;
+#pragma unroll
+        for (int v = 0; v < V; ++v) xq[k - PMAX / 2].v[v] = T(0);
+        if (present) xq[k - PMAX / 2] = ld_keep<T, V>(x + p * V);
+        good = good && present;
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          good = good && emu_ok(ap[k].v[v]) && emu_ok(xq[k - PMAX / 2].v[v]);
+      }
+      if (__all_sync(__activemask(), good)) {
+        float eh = 0.f, el = 0.f;
+#pragma unroll
+        for (int k = PMAX / 2; k < PMAX; ++k)
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            float ah, al, xh, xl;
+            emu_split(ap[k].v[v], ah, al);
+            emu_split(xq[k - PMAX / 2].v[v], xh, xl);
+            emu_fma(ah, al, xh, xl, eh, el);
+          }
+        acc = __dadd_rn(acc, __dadd_rn((double)eh, (double)el));
+      } else {
+        DPacks<(PMAX / 2) * V> dp;
+#pragma unroll
+        for (int k = PMAX / 2; k < PMAX; ++k) {
+          const int64_t p = (int64_t)k * LPR + l;
+          const bool present = ok && p < packs;
+#pragma unroll
+          for (int v = 0; v < V; ++v) {  // absent packs add 0 * 0
+            dp.a[(k - PMAX / 2) * V + v] = present ? (double)ap[k].v[v] : 0.0;
+            dp.x[(k - PMAX / 2) * V + v] = present ? (double)xq[k - PMAX / 2].v[v] : 0.0;
+          }
+        }
+        acc = dfma_fallback(dp, acc);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < PMAX; ++k) {
+        const int64_t p = (int64_t)k * LPR + l;
+        if (ok && p < packs) {
+          const Pack<T, V> xp = ld_keep<T, V>(x + p * V);
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc = fma_rn(ap[k].v[v], xp.v[v], acc);
+        }
       }
     }
     T sum;
@@ -234,7 +345,9 @@ __global__ void __launch_bounds__(kThreads, 4)
 
 template <typename T, int V, bool LONG>
 int launch_long(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
-  auto kern = gemv_row_long_kernel<T, V, kRowLongU, LONG>;
+  // FP64 carries the FP32 emulation of half its products: more work per
+  // byte, so more packs in flight per thread
+  auto kern = gemv_row_long_kernel<T, V, sizeof(T) == 8 ? 2 * kRowLongU : kRowLongU, LONG>;
   const int grid = grid_size((const void*)kern, p.units);
   kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c, p.split, p.kc, p.units);
   return 0;
