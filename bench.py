@@ -348,30 +348,32 @@ def time_sample(work):
 
 # -------------------------------------------------------------- roofline --
 
-def source_sha():
+def source_sha(files=None):
+    """sha256 of the kernel sources (all of csrc/, or the named files)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2108_02025_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    names = sorted(files) if files else sorted(f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h")))
+    for f in names:
+        h.update(f.encode())
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()
 
 
 def measured_traffic(op_name):
-    """DRAM bytes per launch of `op_name` from the committed ncu summary, or
-    None when absent or taken on different kernel sources."""
+    """DRAM bytes per launch of `op_name` from the committed ncu summary
+    (profiles/dram_traffic.json), or None when absent or when the kernel's
+    sources changed since the capture."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None
-    if d.get("source_sha") != source_sha():
-        return None
     k = d.get("kernels", {}).get(op_name)
-    return None if k is None else k.get("dram_bytes_per_launch")
+    if k is None or k.get("sha") != source_sha(k.get("sources")):
+        return None
+    return k.get("dram_bytes_per_launch")
 
 
 def peaks():
