@@ -53,6 +53,15 @@ def _bind(lib):
     lib.oracle_dger.restype = None
     lib.oracle_sger.argtypes = [I, I64, I64, ctypes.c_float, P, P, P, I64]
     lib.oracle_sger.restype = None
+    U8P = ctypes.POINTER(ctypes.c_uint8)
+    lib.oracle_bf16_encode_array.argtypes = [I64, P, P]
+    lib.oracle_bf16_encode_array.restype = None
+    lib.oracle_e4m3_encode_array.argtypes = [I64, P, P]
+    lib.oracle_e4m3_encode_array.restype = None
+    lib.oracle_e4m3_decode_array.argtypes = [I64, P, P]
+    lib.oracle_e4m3_decode_array.restype = None
+    lib.oracle_quantize_e4m3_rows.argtypes = [I64, I64, P, I64, P, I64, P]
+    lib.oracle_quantize_e4m3_rows.restype = None
     lib.oracle_threads.argtypes = []
     lib.oracle_threads.restype = I
     lib.oracle_set_threads.argtypes = [I]
@@ -152,6 +161,43 @@ class Oracle:
                                  _ptr(out), ldc)
         return out
 
+    # ---- reduced-precision storage of A (BF16, E4M3 with per-row scales)
+
+    def bf16_encode(self, v) -> np.ndarray:
+        """FP32 -> BF16 bits, round to nearest even."""
+        v = np.ascontiguousarray(np.asarray(v), dtype=np.float32).ravel()
+        q = np.empty(v.size, dtype=np.uint16)
+        self.lib.oracle_bf16_encode_array(v.size, _ptr(v), _ptr(q))
+        return q
+
+    @staticmethod
+    def bf16_decode(q) -> np.ndarray:
+        """BF16 bits -> FP32 (exact)."""
+        q = np.ascontiguousarray(np.asarray(q), dtype=np.uint16).ravel()
+        return (q.astype(np.uint32) << np.uint32(16)).view(np.float32)
+
+    def e4m3_encode(self, v) -> np.ndarray:
+        """Real values -> E4M3 bits, round to nearest even, saturating at +-448."""
+        v = _f64(v).ravel()
+        q = np.empty(v.size, dtype=np.uint8)
+        self.lib.oracle_e4m3_encode_array(v.size, _ptr(v), _ptr(q))
+        return q
+
+    def e4m3_decode(self, q) -> np.ndarray:
+        q = np.ascontiguousarray(np.asarray(q), dtype=np.uint8).ravel()
+        v = np.empty(q.size, dtype=np.float64)
+        self.lib.oracle_e4m3_decode_array(q.size, _ptr(q), _ptr(v))
+        return v
+
+    def quantize_e4m3_rows(self, m, n, A, lda):
+        """Row-major FP32 A -> (E4M3 bits with leading dimension n, FP32 scales)."""
+        A = np.ascontiguousarray(np.asarray(A), dtype=np.float32).ravel()
+        _check_matrix(ROW_MAJOR, m, n, lda, A.size)
+        Q = np.zeros(max(m * n, 0), dtype=np.uint8)
+        s = np.zeros(max(m, 0), dtype=np.float32)
+        self.lib.oracle_quantize_e4m3_rows(m, n, _ptr(A), lda, _ptr(Q), n, _ptr(s))
+        return Q, s
+
 
 _default = Oracle()
 threads = _default.threads
@@ -161,3 +207,8 @@ gemv_scale = _default.gemv_scale
 dot = _default.dot
 dot_scale = _default.dot_scale
 ger = _default.ger
+bf16_encode = _default.bf16_encode
+bf16_decode = _default.bf16_decode
+e4m3_encode = _default.e4m3_encode
+e4m3_decode = _default.e4m3_decode
+quantize_e4m3_rows = _default.quantize_e4m3_rows

@@ -46,6 +46,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 #include <omp.h>
 
 #if defined(__FAST_MATH__)
@@ -207,4 +208,96 @@ void oracle_sger(int layout, int64_t m, int64_t n, float alpha, const float *x,
       C[k] = fmaf(x[i], t, C[k]);
     }
   }
+}
+
+/* ------------------------------------------------- reduced precision --- */
+/* Storage formats for A in the reduced-precision GEMV (not in the paper,
+   which is FP64/FP32 only; written from the formats' definitions).
+
+   BF16: the upper 16 bits of an IEEE binary32; round to nearest, ties to
+   even, on the 16 dropped bits.  NaN inputs are not defined here.
+
+   E4M3 (OCP 8-bit floating point, "E4M3"): sign, 4 exponent bits with bias
+   7, 3 mantissa bits; normals (-1)^s 2^(e-7) (1 + m/8) for e in 1..15 except
+   e = 15, m = 7 (NaN); subnormals (-1)^s 2^-6 (m/8); largest finite 448.
+   Encoding: round to nearest, ties to even, and saturate to +-448 ("satfinite"). */
+
+uint16_t oracle_bf16_encode(float v) {
+  uint32_t u;
+  memcpy(&u, &v, 4);
+  const uint32_t bias = 0x7FFFu + ((u >> 16) & 1u);  /* ties to even */
+  return (uint16_t)((u + bias) >> 16);
+}
+
+float oracle_bf16_decode(uint16_t q) {
+  const uint32_t u = (uint32_t)q << 16;
+  float v;
+  memcpy(&v, &u, 4);
+  return v;
+}
+
+double oracle_e4m3_decode(uint8_t q) {
+  const int s = q >> 7, e = (q >> 3) & 15, m = q & 7;
+  if (e == 15 && m == 7) return NAN;
+  const double mag = e == 0 ? ldexp((double)m / 8.0, -6) : ldexp(1.0 + (double)m / 8.0, e - 7);
+  return s ? -mag : mag;
+}
+
+/* round half to even of a non-negative value that is an exact multiple of
+   a power of two (no rounding happens in the division below) */
+static double rne(double a) {
+  const double f = floor(a);
+  const double r = a - f;
+  if (r > 0.5) return f + 1.0;
+  if (r < 0.5) return f;
+  return fmod(f, 2.0) == 0.0 ? f : f + 1.0;
+}
+
+uint8_t oracle_e4m3_encode(double v) {
+  if (isnan(v)) return 0x7F;
+  const uint8_t sign = signbit(v) ? 0x80 : 0x00;
+  const double a = fabs(v);
+  if (a >= 448.0) return sign | 0x7E;              /* satfinite */
+  if (a < ldexp(1.0, -6)) {                        /* subnormal grid 2^-9 */
+    const double k = rne(a / ldexp(1.0, -9));      /* 0..8; 8 is the first normal */
+    return sign | (uint8_t)k;
+  }
+  int e;
+  frexp(a, &e);                                    /* a = f 2^e, f in [0.5, 1) */
+  e -= 1;                                          /* a in [2^e, 2^(e+1)) */
+  double k = rne(a / ldexp(1.0, e - 3));           /* 8..16 */
+  if (k == 16.0) { k = 8.0; e += 1; }
+  const int code = ((e + 7) << 3) | ((int)k - 8); /* a < 448 keeps code <= 0x7E */
+  return sign | (uint8_t)code;
+}
+
+void oracle_bf16_encode_array(int64_t n, const float *v, uint16_t *q) {
+  for (int64_t i = 0; i < n; ++i) q[i] = oracle_bf16_encode(v[i]);
+}
+
+void oracle_e4m3_encode_array(int64_t n, const double *v, uint8_t *q) {
+  for (int64_t i = 0; i < n; ++i) q[i] = oracle_e4m3_encode(v[i]);
+}
+
+/* Per-row E4M3 quantisation of a row-major m x n FP32 matrix (leading
+   dimension lda): s_i = fl32(amax_i / 448), q_ij = E4M3(fl32(A_ij / s_i)),
+   all-zero rows get s_i = 0 and q = 0. */
+void oracle_quantize_e4m3_rows(int64_t m, int64_t n, const float *A, int64_t lda, uint8_t *Q,
+                               int64_t ldq, float *scales) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < m; ++i) {
+    float amax = 0.0f;
+    for (int64_t j = 0; j < n; ++j) {
+      const float a = fabsf(A[i * lda + j]);
+      if (a > amax) amax = a;
+    }
+    const float s = amax / 448.0f;
+    scales[i] = s;
+    for (int64_t j = 0; j < n; ++j)
+      Q[i * ldq + j] = s == 0.0f ? 0 : oracle_e4m3_encode((double)(A[i * lda + j] / s));
+  }
+}
+
+void oracle_e4m3_decode_array(int64_t n, const uint8_t *q, double *v) {
+  for (int64_t i = 0; i < n; ++i) v[i] = oracle_e4m3_decode(q[i]);
 }

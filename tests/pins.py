@@ -327,4 +327,79 @@ def pin_thread_count_independent(O):
     assert np.array_equal(res[0][2], res[1][2])
 
 
+
+
+# ----------------------------------------------- reduced-precision A ----
+# Facts of the formats: BF16 is the top half of a binary32 with
+# round-to-nearest-even on the dropped half; E4M3 (OCP FP8) has bias 7, 3
+# mantissa bits, largest finite 448 = 0x7E, smallest normal 2^-6 = 0x08,
+# smallest subnormal 2^-9 = 0x01, NaN 0x7F, and saturating encoding.
+
+def pin_bf16_roundtrip_and_ties(O):
+    codes = np.arange(65536, dtype=np.uint32)
+    vals = (codes << np.uint32(16)).view(np.float32)
+    finite = np.isfinite(vals)
+    assert np.array_equal(O.bf16_encode(vals[finite]), codes[finite].astype(np.uint16))
+    # halfway between code k and k+1 (same sign, k not the largest finite):
+    # ties go to the even code; one unit above or below goes to the nearer
+    k = codes[finite & (codes % 0x8000 != 0x7F7F) & (codes % 0x8000 < 0x7F7F)]
+    half = ((k << np.uint32(16)) | np.uint32(0x8000)).view(np.float32)
+    want = np.where(k % 2 == 0, k, k + 1).astype(np.uint16)
+    assert np.array_equal(O.bf16_encode(half), want)
+    above = ((k << np.uint32(16)) | np.uint32(0x8001)).view(np.float32)
+    below = ((k << np.uint32(16)) | np.uint32(0x7FFF)).view(np.float32)
+    assert np.array_equal(O.bf16_encode(above), (k + 1).astype(np.uint16))
+    assert np.array_equal(O.bf16_encode(below), k.astype(np.uint16))
+    assert O.bf16_encode([1.0, -2.0, np.pi, np.float32(3.4028235e38)]).tolist() == [0x3F80, 0xC000, 0x4049, 0x7F80]
+
+
+def pin_e4m3_known_values(O):
+    enc = O.e4m3_encode([448.0, 2.0 ** -6, 2.0 ** -9, 1.0, -0.0, 0.0, 0.0625, 240.0, -1.75])
+    assert enc.tolist() == [0x7E, 0x08, 0x01, 0x38, 0x80, 0x00, 0x18, 0x77, 0xBE]
+    dec = O.e4m3_decode(np.arange(256, dtype=np.uint8))
+    assert np.isnan(dec[0x7F]) and np.isnan(dec[0xFF])
+    pos = dec[:0x7F]
+    assert np.all(np.diff(pos) > 0)                 # strictly increasing codes 0..0x7E
+    assert pos[-1] == 448.0 and pos[1] == 2.0 ** -9 and pos[8] == 2.0 ** -6
+    assert np.array_equal(dec[0x80:0xFF], -pos)     # sign-magnitude
+    # spacing is constant inside a binade: 2^(e-3) for e >= -6, 2^-9 below
+    for e in range(-6, 9):
+        lo, hi = 2.0 ** e, min(2.0 ** (e + 1), 448.0)
+        inside = pos[(pos >= lo) & (pos <= hi)]
+        assert np.allclose(np.diff(inside), 2.0 ** (e - 3))
+
+
+def pin_e4m3_roundtrip_ties_saturation(O):
+    codes = np.array([c for c in range(256) if c not in (0x7F, 0xFF)], dtype=np.uint8)
+    assert np.array_equal(O.e4m3_encode(O.e4m3_decode(codes)), codes)
+    pos = O.e4m3_decode(np.arange(0x7F, dtype=np.uint8))
+    mid = (pos[:-1] + pos[1:]) / 2                   # exact in binary64
+    k = np.arange(0x7E)
+    assert np.array_equal(O.e4m3_encode(mid), np.where(k % 2 == 0, k, k + 1).astype(np.uint8))
+    assert np.array_equal(O.e4m3_encode(np.nextafter(mid, 0)), k.astype(np.uint8))
+    assert np.array_equal(O.e4m3_encode(np.nextafter(mid, 1e9)), (k + 1).astype(np.uint8))
+    assert O.e4m3_encode([448.0001, 464.0, 470.0, 1e30, np.inf, -1e30]).tolist() == [0x7E, 0x7E, 0x7E, 0x7E, 0x7E, 0xFE]
+    assert O.e4m3_encode([2.0 ** -10, 2.0 ** -10 * 1.0001, 3 * 2.0 ** -10]).tolist() == [0, 1, 2]
+
+
+def pin_quantize_e4m3_rows(O):
+    m, n = 6, 40
+    A = synth.uniform(m * n, 131, 1, np.float32).reshape(m, n)
+    A[0] *= 448.0 / np.abs(A[0]).max()              # amax 448: scale exactly 1
+    A[1] = 0.0                                      # all-zero row: scale 0, codes 0
+    A[2] *= 1e-3
+    A[3] *= 1e3
+    Q, s = O.quantize_e4m3_rows(m, n, A.ravel(), n)
+    Q = Q.reshape(m, n)
+    assert s[0] == 1.0 and np.array_equal(Q[0], O.e4m3_encode(A[0].astype(np.float64)))
+    assert s[1] == 0.0 and not Q[1].any()
+    for i in (2, 3, 4, 5):
+        amax = np.abs(A[i]).max()
+        assert s[i] == np.float32(amax) / np.float32(448.0)
+        assert np.abs(O.e4m3_decode(Q[i])).max() == 448.0      # the largest element maps to 448
+        deq = O.e4m3_decode(Q[i]) * np.float64(s[i])
+        # half a unit of the 3-bit mantissa, or the subnormal floor
+        assert np.all(np.abs(deq - A[i]) <= np.maximum(2.0 ** -4 * np.abs(A[i]), s[i] * 2.0 ** -10) * 1.0000001)
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

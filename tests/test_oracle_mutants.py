@@ -44,6 +44,17 @@ MUTANTS = {
         "double t = alpha * y[j];", "double t = y[j];"),
     "sger_double_rounding": (
         "C[k] = fmaf(x[i], t, C[k]);", "C[k] = x[i] * t + C[k];"),
+    "bf16_ties_always_down": (
+        "const uint32_t bias = 0x7FFFu + ((u >> 16) & 1u);", "const uint32_t bias = 0x7FFFu;"),
+    "e4m3_ties_half_up": (
+        "  if (r < 0.5) return f;\n  return fmod(f, 2.0) == 0.0 ? f : f + 1.0;",
+        "  if (r < 0.5) return f;\n  return f + 1.0;"),
+    "e4m3_no_saturation": (
+        "if (a >= 448.0) return sign | 0x7E;", "if (a >= 480.0) return sign | 0x7E;"),
+    "e4m3_wrong_exponent_bias": (
+        "const int code = ((e + 7) << 3)", "const int code = ((e + 8) << 3)"),
+    "e4m3_scale_not_amax": (
+        "const float s = amax / 448.0f;", "const float s = amax / 256.0f;"),
     "gemv_scale_signed_sum": (
         "s = s + fabs(A[idx(layout, i, j, lda)] * x[j]);",
         "s = s + A[idx(layout, i, j, lda)] * x[j];"),
