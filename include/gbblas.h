@@ -76,7 +76,13 @@ extern "C" {
 #endif
 
 typedef enum { GB_ROW_MAJOR = 0, GB_COL_MAJOR = 1 } gb_layout;
-typedef enum { GB_OP_GEMV = 0, GB_OP_DOT = 1, GB_OP_GER = 2 } gb_op;
+typedef enum {
+  GB_OP_GEMV = 0,
+  GB_OP_DOT = 1,
+  GB_OP_GER = 2,
+  GB_OP_GEMV_BF16 = 3, /* gb_gemv_bf16 (dtype ignored, row-major only) */
+  GB_OP_GEMV_E4M3 = 4  /* gb_gemv_e4m3 (dtype ignored, row-major only) */
+} gb_op;
 typedef enum { GB_F32 = 0, GB_F64 = 1 } gb_dtype;
 
 enum {
@@ -159,6 +165,47 @@ int gb_dger(int layout, int64_t m, int64_t n, double alpha, const double *x, con
             double *C, int64_t ldc, gb_stream stream);
 int gb_sger(int layout, int64_t m, int64_t n, float alpha, const float *x, const float *y,
             float *C, int64_t ldc, gb_stream stream);
+
+/* Reduced-precision storage of A (not in the paper, whose GEMV is FP64 /
+   FP32): fewer bytes of A per product for the HBM-bound GEMV.  Row-major
+   only; x and c stay FP32.
+
+   gb_quantize_bf16: Q_ij = BF16(A_ij), the top 16 bits of the binary32
+   rounded to nearest, ties to even.
+     m, n (args 1, 2); A device FP32, row-major, lda >= max(1,n) (args 3, 4);
+     Q device uint16 output, ldq >= max(1,n), not overlapping A (args 5, 6);
+     stream (arg 7).
+   gb_quantize_e4m3: per row i, s_i = fl32(amax_j |A_ij| / 448) and
+   Q_ij = E4M3(fl32(A_ij / s_i)), OCP FP8 E4M3 (bias 7, 3 mantissa bits),
+   round to nearest even, saturating at +-448; an all-zero row gets s_i = 0
+   and codes 0.  A must be finite.
+     m, n (1, 2); A, lda (3, 4); Q device uint8 output, ldq (5, 6);
+     scales device FP32 output of m values (7); stream (8). */
+int gb_quantize_bf16(int64_t m, int64_t n, const float *A, int64_t lda, uint16_t *Q, int64_t ldq,
+                     gb_stream stream);
+int gb_quantize_e4m3(int64_t m, int64_t n, const float *A, int64_t lda, uint8_t *Q, int64_t ldq,
+                     float *scales, gb_stream stream);
+
+/* GEMV with A stored in reduced precision:
+     c_i <- c_i + alpha * s_i * sum_j Q_ij x_j   (s_i = 1 for BF16)
+   The products are FP32 fmas of the exactly decoded codes with x, in chains
+   of at most 32 folded into a compensated FP32 sum, then a fixed-order FP32
+   block sum (split partials in FP64).  Row-major Q with 16-byte aligned
+   rows (Q 16-byte aligned, ldq * element bytes a multiple of 16) and x
+   16-byte aligned; otherwise the argument is reported invalid.  E4M3 codes
+   0x7F and 0xFF (NaN) are not supported in Q (the quantiser never writes
+   them).
+   gb_gemv_bf16: m, n (1, 2); alpha (3); Q uint16, ldq (4, 5); x (6);
+     c (7); ws, ws_bytes (8, 9) sized by gb_workspace_bytes(GB_OP_GEMV_BF16,
+     0, GB_ROW_MAJOR, m, n); stream (10).
+   gb_gemv_e4m3: m, n (1, 2); alpha (3); Q uint8, ldq (4, 5); scales (6);
+     x (7); c (8); ws, ws_bytes (9, 10) sized by
+     gb_workspace_bytes(GB_OP_GEMV_E4M3, ...); stream (11). */
+int gb_gemv_bf16(int64_t m, int64_t n, float alpha, const uint16_t *Q, int64_t ldq,
+                 const float *x, float *c, void *ws, size_t ws_bytes, gb_stream stream);
+int gb_gemv_e4m3(int64_t m, int64_t n, float alpha, const uint8_t *Q, int64_t ldq,
+                 const float *scales, const float *x, float *c, void *ws, size_t ws_bytes,
+                 gb_stream stream);
 
 /* GEMV without allocation.  The paper has no counterpart: this entry point
    exists for callers that cannot allocate device memory (code running where

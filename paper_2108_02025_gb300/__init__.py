@@ -23,7 +23,7 @@ LIB_PATH = os.environ.get("GBBLAS_LIB", os.path.join(os.path.dirname(os.path.abs
                                                      "libgbblas.so"))
 
 ROW_MAJOR, COL_MAJOR = 0, 1
-OP_GEMV, OP_DOT, OP_GER = 0, 1, 2
+OP_GEMV, OP_DOT, OP_GER, OP_GEMV_BF16, OP_GEMV_E4M3 = 0, 1, 2, 3, 4
 F32, F64 = 0, 1
 
 GB_OK = 0
@@ -57,8 +57,13 @@ def _load() -> ctypes.CDLL:
     lib.gb_dger.argtypes = [I, I64, I64, D, P, P, P, I64, P]
     lib.gb_sger.argtypes = [I, I64, I64, F, P, P, P, I64, P]
     lib.gb_dgemv_noalloc.argtypes = [I, I64, I64, D, P, I64, P, P, P]
+    lib.gb_quantize_bf16.argtypes = [I64, I64, P, I64, P, I64, P]
+    lib.gb_quantize_e4m3.argtypes = [I64, I64, P, I64, P, I64, P, P]
+    lib.gb_gemv_bf16.argtypes = [I64, I64, F, P, I64, P, P, P, SZ, P]
+    lib.gb_gemv_e4m3.argtypes = [I64, I64, F, P, I64, P, P, P, P, SZ, P]
     for name in ("gb_dgemv", "gb_sgemv", "gb_ddot", "gb_sdot", "gb_dger", "gb_sger",
-                 "gb_dgemv_noalloc"):
+                 "gb_dgemv_noalloc", "gb_quantize_bf16", "gb_quantize_e4m3", "gb_gemv_bf16",
+                 "gb_gemv_e4m3"):
         getattr(lib, name).restype = I
     return lib
 
@@ -68,7 +73,8 @@ _lib = _load()
 # Every symbol the header declares (checked by the tests against include/gbblas.h).
 EXPORTS = ("gb_version", "gb_status_string", "gb_workspace_bytes", "gb_workspace_init",
            "gb_dgemv", "gb_sgemv", "gb_ddot", "gb_sdot", "gb_dger", "gb_sger",
-           "gb_dgemv_noalloc")
+           "gb_dgemv_noalloc", "gb_quantize_bf16", "gb_quantize_e4m3", "gb_gemv_bf16",
+           "gb_gemv_e4m3")
 
 
 def lib() -> ctypes.CDLL:
@@ -137,6 +143,24 @@ def gb_dger(layout, m, n, alpha, x, y, C, ldc, stream=None) -> int:
 
 def gb_sger(layout, m, n, alpha, x, y, C, ldc, stream=None) -> int:
     return _lib.gb_sger(layout, m, n, alpha, _ptr(x), _ptr(y), _ptr(C), ldc, _stream(stream))
+
+
+def gb_quantize_bf16(m, n, A, lda, Q, ldq, stream=None) -> int:
+    return _lib.gb_quantize_bf16(m, n, _ptr(A), lda, _ptr(Q), ldq, _stream(stream))
+
+
+def gb_quantize_e4m3(m, n, A, lda, Q, ldq, scales, stream=None) -> int:
+    return _lib.gb_quantize_e4m3(m, n, _ptr(A), lda, _ptr(Q), ldq, _ptr(scales), _stream(stream))
+
+
+def gb_gemv_bf16(m, n, alpha, Q, ldq, x, c, ws, ws_bytes, stream=None) -> int:
+    return _lib.gb_gemv_bf16(m, n, alpha, _ptr(Q), ldq, _ptr(x), _ptr(c), _ptr(ws), ws_bytes,
+                             _stream(stream))
+
+
+def gb_gemv_e4m3(m, n, alpha, Q, ldq, scales, x, c, ws, ws_bytes, stream=None) -> int:
+    return _lib.gb_gemv_e4m3(m, n, alpha, _ptr(Q), ldq, _ptr(scales), _ptr(x), _ptr(c), _ptr(ws),
+                             ws_bytes, _stream(stream))
 
 
 def gb_dgemv_noalloc(layout, m, n, alpha, A, lda, x, c, stream=None) -> int:
@@ -225,3 +249,36 @@ def ger(x, y, C, alpha: float = 1.0, layout: int = ROW_MAJOR, m: int | None = No
     dt = _dtype_code(C)
     f = gb_dger if dt == F64 else gb_sger
     _check(f(layout, m, n, alpha, x, y, C, ldc, stream), "ger")
+
+
+def quantize(A, fmt: str, stream=None):
+    """Row-major 2-D FP32 CUDA tensor -> (codes, scales or None); fmt 'bf16' or
+    'e4m3'.  The code rows are padded to 16 bytes (the GEMV reads columns < n)."""
+    import torch
+    m, n = A.shape
+    assert A.dtype == torch.float32 and A.stride(1) == 1
+    if fmt == "bf16":
+        ldq = (n + 7) // 8 * 8  # 16-byte rows
+        Q = torch.empty((m, ldq), dtype=torch.int16, device=A.device)
+        _check(gb_quantize_bf16(m, n, A, A.stride(0), Q, ldq, stream), "quantize_bf16")
+        return Q, None
+    ldq = (n + 15) // 16 * 16
+    Q = torch.empty((m, ldq), dtype=torch.uint8, device=A.device)
+    s = torch.empty(m, dtype=torch.float32, device=A.device)
+    _check(gb_quantize_e4m3(m, n, A, A.stride(0), Q, ldq, s, stream), "quantize_e4m3")
+    return Q, s
+
+
+def gemv_q(Q, scales, x, c, alpha: float = 1.0, n: int | None = None, stream=None) -> None:
+    """c += alpha * dequant(Q) @ x for codes from ``quantize`` (BF16 if scales is None)."""
+    m = Q.shape[0]
+    ldq = Q.stride(0)
+    n = Q.shape[1] if n is None else n
+    if scales is None:
+        nb = gb_workspace_bytes(OP_GEMV_BF16, 0, ROW_MAJOR, m, n)
+        ws = workspace(nb, Q.device, stream)
+        _check(gb_gemv_bf16(m, n, alpha, Q, ldq, x, c, ws, nb, stream), "gemv_bf16")
+    else:
+        nb = gb_workspace_bytes(OP_GEMV_E4M3, 0, ROW_MAJOR, m, n)
+        ws = workspace(nb, Q.device, stream)
+        _check(gb_gemv_e4m3(m, n, alpha, Q, ldq, scales, x, c, ws, nb, stream), "gemv_e4m3")

@@ -262,6 +262,17 @@ size_t dot_ws(size_t e, int64_t n) {
   return b;
 }
 
+// Reduced-precision GEMV (row-major): per-row counters, like the long-row
+// FP32 kernel; `per` elements per 16-byte pack.
+inline SplitShape qgemv_shape(int fmt, int64_t m, int64_t n) {
+  const int64_t per = fmt == 0 ? 8 : 16;
+  const int64_t quantum = 256 * per;
+  SplitShape s = block_split(m, n, quantum * kQuantU, quantum, 4);
+  s.G = s.S;
+  s.NG = 1;
+  return s;
+}
+
 // ------------------------------------------------------- fault injection ---
 
 struct Inject {
@@ -403,6 +414,34 @@ int ger(int layout, int64_t m, int64_t n, T alpha, const T* x, const T* y, T* C,
   return cuda_status();
 }
 
+// Shared checks of the reduced-precision GEMV entry points.
+int qgemv(int fmt, int64_t m, int64_t n, float alpha, const void* Q, int64_t ldq,
+          const float* scales, const float* x, float* c, void* ws, size_t ws_bytes,
+          gb_stream stream) {
+  const int64_t bytes = fmt == 0 ? 2 : 1;
+  const int k = fmt == 0 ? 0 : 1;  // E4M3 has the extra scales argument
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (ldq < (n > 1 ? n : 1) || (ldq * bytes) % 16 != 0) return -5;
+  if (m == 0 || n == 0 || alpha == 0.f) return GB_OK;
+  if (!Q || !aligned16(Q)) return -4;
+  if (fmt == 1 && !scales) return -6;
+  if (!x || !aligned16(x)) return -(6 + k);
+  if (!c) return -(7 + k);
+  const unsigned __int128 cb = (unsigned __int128)m * 4;
+  if (overlap(c, cb, Q, matrix_bytes(GB_ROW_MAJOR, m, n, ldq, (size_t)bytes)) ||
+      overlap(c, cb, x, (unsigned __int128)n * 4) || (fmt == 1 && overlap(c, cb, scales, cb)))
+    return -(7 + k);
+  const SplitShape s = qgemv_shape(fmt, m, n);
+  const size_t need = split_bytes(s, m);
+  if (need > 0 && (!ws || !aligned16(ws))) return -(8 + k);
+  if (ws_bytes < need) return GB_ERR_WORKSPACE;
+  if (injected(GB_OP_GEMV)) return GB_ERR_INJECTED;
+  gemv_q_launch(fmt, m, n, alpha, Q, ldq, scales, x, c, split_view(s, m, ws), s.kc, s.items * s.S,
+                static_cast<cudaStream_t>(stream));
+  return cuda_status();
+}
+
 }  // namespace
 
 // Occupancy of each kernel is queried once per (kernel, device).
@@ -474,9 +513,13 @@ const char* gb_status_string(int status) {
 }
 
 size_t gb_workspace_bytes(int op, int dtype, int layout, int64_t m, int64_t n) {
-  if (dtype != GB_F32 && dtype != GB_F64) return 0;
+  if (op != GB_OP_GEMV_BF16 && op != GB_OP_GEMV_E4M3 && dtype != GB_F32 && dtype != GB_F64) return 0;
   const size_t e = dtype == GB_F32 ? 4 : 8;
   if (op == GB_OP_DOT) return n > 0 ? gb::dot_ws(e, n) : 0;
+  if (op == GB_OP_GEMV_BF16 || op == GB_OP_GEMV_E4M3) {
+    if (layout != GB_ROW_MAJOR || m <= 0 || n <= 0) return 0;
+    return gb::split_bytes(gb::qgemv_shape(op == GB_OP_GEMV_BF16 ? 0 : 1, m, n), m);
+  }
   if (op == GB_OP_GEMV) {
     if (layout != GB_ROW_MAJOR && layout != GB_COL_MAJOR) return 0;
     if (m <= 0 || n <= 0) return 0;
@@ -521,6 +564,57 @@ int gb_dger(int layout, int64_t m, int64_t n, double alpha, const double* x, con
 int gb_sger(int layout, int64_t m, int64_t n, float alpha, const float* x, const float* y,
             float* C, int64_t ldc, gb_stream stream) {
   return gb::ger<float>(layout, m, n, alpha, x, y, C, ldc, stream);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------ reduced precision of A ---
+
+extern "C" {
+
+int gb_quantize_bf16(int64_t m, int64_t n, const float* A, int64_t lda, uint16_t* Q, int64_t ldq,
+                     gb_stream stream) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (lda < (n > 1 ? n : 1)) return -4;
+  if (ldq < (n > 1 ? n : 1)) return -6;
+  if (m == 0 || n == 0) return GB_OK;
+  if (!A) return -3;
+  if (!Q) return -5;
+  if (gb::overlap(Q, gb::matrix_bytes(GB_ROW_MAJOR, m, n, ldq, 2), A, gb::matrix_bytes(GB_ROW_MAJOR, m, n, lda, 4)))
+    return -5;
+  gb::quantize_bf16_launch(m, n, A, lda, Q, ldq, static_cast<cudaStream_t>(stream));
+  return gb::cuda_status();
+}
+
+int gb_quantize_e4m3(int64_t m, int64_t n, const float* A, int64_t lda, uint8_t* Q, int64_t ldq,
+                     float* scales, gb_stream stream) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (lda < (n > 1 ? n : 1)) return -4;
+  if (ldq < (n > 1 ? n : 1)) return -6;
+  if (m == 0 || n == 0) return GB_OK;
+  if (!A) return -3;
+  if (!Q) return -5;
+  if (!scales) return -7;
+  const unsigned __int128 ab = gb::matrix_bytes(GB_ROW_MAJOR, m, n, lda, 4);
+  if (gb::overlap(Q, gb::matrix_bytes(GB_ROW_MAJOR, m, n, ldq, 1), A, ab)) return -5;
+  if (gb::overlap(scales, (unsigned __int128)m * 4, A, ab) ||
+      gb::overlap(scales, (unsigned __int128)m * 4, Q, gb::matrix_bytes(GB_ROW_MAJOR, m, n, ldq, 1)))
+    return -7;
+  gb::quantize_e4m3_launch(m, n, A, lda, Q, ldq, scales, static_cast<cudaStream_t>(stream));
+  return gb::cuda_status();
+}
+
+int gb_gemv_bf16(int64_t m, int64_t n, float alpha, const uint16_t* Q, int64_t ldq,
+                 const float* x, float* c, void* ws, size_t ws_bytes, gb_stream stream) {
+  return gb::qgemv(0, m, n, alpha, Q, ldq, nullptr, x, c, ws, ws_bytes, stream);
+}
+
+int gb_gemv_e4m3(int64_t m, int64_t n, float alpha, const uint8_t* Q, int64_t ldq,
+                 const float* scales, const float* x, float* c, void* ws, size_t ws_bytes,
+                 gb_stream stream) {
+  return gb::qgemv(1, m, n, alpha, Q, ldq, scales, x, c, ws, ws_bytes, stream);
 }
 
 }  // extern "C"

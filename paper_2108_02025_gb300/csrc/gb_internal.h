@@ -25,6 +25,7 @@ struct GemvArgs {
 constexpr int kRowLongU = 4;     // packs in flight per thread, long-row kernel
 constexpr int kRowScalarRW = 4;  // rows per lane group, misaligned row-major kernel
 constexpr int kColTileU = 8;     // columns in flight per thread, column-major tile kernel
+constexpr int kQuantU = 2;       // 16-byte packs in flight per thread, BF16 / E4M3 GEMV
 
 // How one GEMV is cut into work.  The kernel, the split S and the per-thread
 // summation order depend only on (dtype, layout, m, n) and on the pointer
@@ -89,5 +90,14 @@ template <typename T>
 int dot_launch(const DotArgs<T>& a, const DotPlan& p, cudaStream_t st);
 template <typename T>
 int ger_launch(const GerArgs<T>& a, const GerPlan& p, cudaStream_t st);
+
+int quantize_bf16_launch(int64_t m, int64_t n, const float* A, int64_t lda, uint16_t* Q,
+                         int64_t ldq, cudaStream_t st);
+int quantize_e4m3_launch(int64_t m, int64_t n, const float* A, int64_t lda, uint8_t* Q,
+                         int64_t ldq, float* scales, cudaStream_t st);
+// fmt 0: BF16, 1: E4M3 with per-row scales
+int gemv_q_launch(int fmt, int64_t m, int64_t n, float alpha, const void* Q, int64_t ldq,
+                  const float* scales, const float* x, float* c, const Split& sp, int64_t kc,
+                  int64_t units, cudaStream_t st);
 
 }  // namespace gb

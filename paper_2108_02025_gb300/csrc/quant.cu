@@ -1,0 +1,236 @@
+// Reduced-precision storage of A for GEMV: BF16, and FP8 E4M3 with one FP32
+// scale per row.  Not in the paper (its GEMV is FP64/FP32); fewer bytes of A
+// per product is the lever on an HBM-bound GEMV.
+//
+// * quantisers: BF16 = binary32 rounded to its top 16 bits (nearest, ties
+//   to even); E4M3 (OCP FP8: bias 7, 3 mantissa bits, largest finite 448)
+//   with s_i = fl32(amax_i / 448) and q_ij = E4M3_rne_satfinite(fl32(A_ij /
+//   s_i)); all-zero rows get s_i = 0 and codes 0.
+// * GEMV: c_i <- c_i + alpha * s_i * sum_j q_ij x_j (s_i = 1 for BF16), x
+//   and c FP32.  Row-major only, streamed like the FP32 long-row kernel (a
+//   block per (row, chunk) unit, consecutive units per block); products are
+//   FP32 fmas in chains of at most 32, folded into a compensated FP32 sum
+//   (TwoSum), then a fixed-order block sum.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "gb_common.cuh"
+#include "gb_internal.h"
+
+namespace gb {
+namespace {
+
+// ------------------------------------------------------------- decoders ---
+
+// BF16 bits -> FP32 (exact).
+__device__ __forceinline__ float bf16_bits_to_float(unsigned b) { return __uint_as_float(b << 16); }
+
+// E4M3 bits -> FP32 (exact).  The 7 magnitude bits, moved to the top of a
+// binary32 exponent/mantissa field, are the E4M3 value times 2^-120 for
+// normals and for subnormals alike (an FP32 subnormal in the second case),
+// so one multiplication by 2^120 finishes the job.  The NaN codes 0x7F and
+// 0xFF, which the quantiser never writes, are not decoded as NaN.
+__device__ __forceinline__ float e4m3_bits_to_float(unsigned b) {
+  const float v = __fmul_rn(__uint_as_float((b & 0x7Fu) << 20), 0x1p120f);
+  return __uint_as_float(__float_as_uint(v) | ((b & 0x80u) << 24));
+}
+
+template <int FMT>  // 0: BF16 (8 per 16-byte pack), 1: E4M3 (16 per pack)
+struct Fmt {
+  static constexpr int PER = FMT == 0 ? 8 : 16;  // elements per 16-byte pack
+  static constexpr int BYTES = FMT == 0 ? 2 : 1;
+};
+
+// Element k of a 16-byte pack held as 4 words.
+template <int FMT>
+__device__ __forceinline__ float unpack(const uint4& w, int k) {
+  const unsigned word = k < Fmt<FMT>::PER / 4 ? w.x : k < Fmt<FMT>::PER / 2 ? w.y : k < 3 * Fmt<FMT>::PER / 4 ? w.z : w.w;
+  if constexpr (FMT == 0) {
+    const int h = k & 1;
+    return bf16_bits_to_float(h ? word >> 16 : word & 0xFFFFu);
+  } else {
+    const int b = k & 3;
+    return e4m3_bits_to_float((word >> (8 * b)) & 0xFFu);
+  }
+}
+
+// ------------------------------------------------------------ quantisers ---
+
+__global__ void __launch_bounds__(kThreads)
+    quantize_bf16_kernel(int64_t m, int64_t n, const float* __restrict__ A, int64_t lda,
+                         uint16_t* __restrict__ Q, int64_t ldq) {
+  const int64_t total = m * n;
+  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * kThreads) {
+    const int64_t i = e / n, j = e - i * n;
+    const __nv_bfloat16 b = __float2bfloat16_rn(__ldcs(A + i * lda + j));
+    Q[i * ldq + j] = *reinterpret_cast<const uint16_t*>(&b);
+  }
+}
+
+// One block per row: the row's absolute maximum, then the codes.
+__global__ void __launch_bounds__(kThreads)
+    quantize_e4m3_kernel(int64_t m, int64_t n, const float* __restrict__ A, int64_t lda,
+                         uint8_t* __restrict__ Q, int64_t ldq, float* __restrict__ scales) {
+  __shared__ float red[kThreads / 32];
+  for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+    const float* Ar = A + i * lda;
+    float amax = 0.f;
+    for (int64_t j = threadIdx.x; j < n; j += kThreads) amax = fmaxf(amax, fabsf(Ar[j]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+    __syncthreads();
+    amax = 0.f;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) amax = fmaxf(amax, red[w]);
+    const float s = __fdiv_rn(amax, 448.0f);
+    if (threadIdx.x == 0) scales[i] = s;
+    for (int64_t j = threadIdx.x; j < n; j += kThreads) {
+      uint8_t q = 0;
+      if (s != 0.f) q = (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(Ar[j], s), __NV_SATFINITE, __NV_E4M3);
+      Q[i * ldq + j] = q;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ GEMV ---
+
+// unit u = (row u / S, chunk u % S); block b takes units [b*U/G, (b+1)*U/G)
+template <int FMT, int U>
+__global__ void __launch_bounds__(kThreads, 4)
+    gemv_q_kernel(int64_t m, int64_t n, float alpha, const unsigned char* __restrict__ Q,
+                  int64_t ldq_bytes, const float* __restrict__ scales, const float* __restrict__ x,
+                  float* __restrict__ c, const Split sp, int64_t KC, int64_t units) {
+  constexpr int PER = Fmt<FMT>::PER;
+  constexpr int64_t STEP = (int64_t)kThreads * PER;      // columns per pack position
+  constexpr int CHAIN = 32 / (U * PER) > 0 ? 32 / (U * PER) : 1;  // bodies per FP32 chain
+  __shared__ float red[kThreads / 32];
+  __shared__ double red_d[kThreads / 32];
+  __shared__ int flag;
+
+  const int S = sp.S;
+  const int64_t u0 = units * blockIdx.x / gridDim.x;
+  const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
+  for (int64_t u = u0; u < u1; ++u) {
+    const int64_t row = u / S;
+    const int s = (int)(u - row * S);
+    const int64_t k0 = (int64_t)s * KC;
+    const int64_t k1 = (k0 + KC < n) ? k0 + KC : n;
+    const int64_t kv1 = k0 + ((k1 - k0) / PER) * PER;
+    const unsigned char* Qr = Q + row * ldq_bytes;
+
+    float acc = 0.f, hi = 0.f, lo = 0.f;
+    int chain = 0;
+    int64_t j = k0 + (int64_t)threadIdx.x * PER;
+#pragma unroll 1
+    for (; j + (U - 1) * STEP < kv1; j += U * STEP) {
+      uint4 qp[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q)
+        qp[q] = __ldcs(reinterpret_cast<const uint4*>(Qr + (j + q * STEP) * Fmt<FMT>::BYTES));
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+#pragma unroll
+        for (int k4 = 0; k4 < PER; k4 += 4) {
+          const float4 xv = __ldg(reinterpret_cast<const float4*>(x + j + q * STEP + k4));
+          acc = __fmaf_rn(unpack<FMT>(qp[q], k4 + 0), xv.x, acc);
+          acc = __fmaf_rn(unpack<FMT>(qp[q], k4 + 1), xv.y, acc);
+          acc = __fmaf_rn(unpack<FMT>(qp[q], k4 + 2), xv.z, acc);
+          acc = __fmaf_rn(unpack<FMT>(qp[q], k4 + 3), xv.w, acc);
+        }
+      }
+      if (++chain == CHAIN) {  // fold the chain (at most 32 products) into (hi, lo)
+        chain = 0;
+        float e;
+        two_sum_f(hi, acc, hi, e);
+        lo = __fadd_rn(lo, e);
+        acc = 0.f;
+      }
+    }
+#pragma unroll 1
+    for (; j < kv1; j += STEP) {  // remaining whole packs, one at a time
+      const uint4 qv = __ldcs(reinterpret_cast<const uint4*>(Qr + j * Fmt<FMT>::BYTES));
+      float a2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < PER; ++k) a2 = __fmaf_rn(unpack<FMT>(qv, k), __ldg(x + j + k), a2);
+      float e;
+      two_sum_f(hi, a2, hi, e);
+      lo = __fadd_rn(lo, e);
+    }
+    if (kv1 + threadIdx.x < k1) {  // ragged end (< PER columns)
+      const int64_t jj = kv1 + threadIdx.x;
+      const unsigned b = FMT == 0 ? (unsigned)reinterpret_cast<const uint16_t*>(Qr)[jj] : (unsigned)Qr[jj];
+      const float qv = FMT == 0 ? bf16_bits_to_float(b) : e4m3_bits_to_float(b);
+      acc = __fmaf_rn(qv, __ldg(x + jj), acc);
+    }
+    float v = hi + (lo + acc);
+
+    // fixed-order block sum (warp butterfly, then warps in order) in FP32
+    v = group_sum_f<32>(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float total = 0.f;
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) total = __fadd_rn(total, red[w]);
+    }
+    const float sc = FMT == 1 ? scales[row] : 1.f;
+    if (S == 1) {
+      if (threadIdx.x == 0) c[row] = __fmaf_rn(alpha, __fmul_rn(sc, total), c[row]);
+    } else {
+      if (threadIdx.x == 0) sp.part[(int64_t)s * m + row] = (double)total;
+      if (arrive_last(sp.tickets + row, (unsigned)S, &flag)) {
+        double p = 0.0;
+        for (int q = threadIdx.x; q < S; q += kThreads) p = __dadd_rn(p, __ldcg(sp.part + (int64_t)q * m + row));
+        p = group_sum<32>(p);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red_d[threadIdx.x >> 5] = p;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double t = 0.0;
+#pragma unroll
+          for (int w = 0; w < kThreads / 32; ++w) t = __dadd_rn(t, red_d[w]);
+          c[row] = __fmaf_rn(alpha, __fmul_rn(sc, (float)t), c[row]);
+          sp.tickets[row] = 0u;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int quantize_bf16_launch(int64_t m, int64_t n, const float* A, int64_t lda, uint16_t* Q,
+                         int64_t ldq, cudaStream_t st) {
+  const int grid = grid_size((const void*)quantize_bf16_kernel, (m * n + kThreads - 1) / kThreads);
+  quantize_bf16_kernel<<<grid, kThreads, 0, st>>>(m, n, A, lda, Q, ldq);
+  return 0;
+}
+
+int quantize_e4m3_launch(int64_t m, int64_t n, const float* A, int64_t lda, uint8_t* Q,
+                         int64_t ldq, float* scales, cudaStream_t st) {
+  const int grid = grid_size((const void*)quantize_e4m3_kernel, m);
+  quantize_e4m3_kernel<<<grid, kThreads, 0, st>>>(m, n, A, lda, Q, ldq, scales);
+  return 0;
+}
+
+int gemv_q_launch(int fmt, int64_t m, int64_t n, float alpha, const void* Q, int64_t ldq,
+                  const float* scales, const float* x, float* c, const Split& sp, int64_t kc,
+                  int64_t units, cudaStream_t st) {
+  const unsigned char* q = static_cast<const unsigned char*>(Q);
+  if (fmt == 0) {
+    auto kern = gemv_q_kernel<0, kQuantU>;
+    const int grid = grid_size((const void*)kern, units);
+    kern<<<grid, kThreads, 0, st>>>(m, n, alpha, q, ldq * 2, scales, x, c, sp, kc, units);
+  } else {
+    auto kern = gemv_q_kernel<1, kQuantU>;
+    const int grid = grid_size((const void*)kern, units);
+    kern<<<grid, kThreads, 0, st>>>(m, n, alpha, q, ldq, scales, x, c, sp, kc, units);
+  }
+  return 0;
+}
+
+}  // namespace gb

@@ -3,9 +3,11 @@
     python -m paper_2108_02025_gb300.run_case gemv f32 row 64 1048576 [--reps 20]
     python -m paper_2108_02025_gb300.run_case dot f64 - 1 268435456
     python -m paper_2108_02025_gb300.run_case ger f64 col 16384 16384
+    python -m paper_2108_02025_gb300.run_case gemvq e4m3 row 32768 32768
 
 Inputs are uniform[-1,1] from the synth generator (seed 0), written on the
-device.  Each call is timed with CUDA events on the launching stream; the
+device; for ``gemvq`` (A stored as BF16 or E4M3 with per-row scales) A is
+N(0,1) with rows scaled by 10^U[-3,3], quantised before timing.  Each call is timed with CUDA events on the launching stream; the
 median is reported with the algorithmic bytes (every element touched once)
 per second.  Used to profile one kernel in isolation.
 """
@@ -24,8 +26,8 @@ if ROOT not in sys.path:
 
 def main(argv=None):
     p = argparse.ArgumentParser(description="one GEMV / DOT / GER case")
-    p.add_argument("op", choices=["gemv", "dot", "ger"])
-    p.add_argument("dtype", choices=["f32", "f64"])
+    p.add_argument("op", choices=["gemv", "dot", "ger", "gemvq"])
+    p.add_argument("dtype", choices=["f32", "f64", "bf16", "e4m3"])
     p.add_argument("layout", choices=["row", "col", "-"])
     p.add_argument("m", type=int)
     p.add_argument("n", type=int)
@@ -36,8 +38,8 @@ def main(argv=None):
     import paper_2108_02025_gb300 as gb
     import synth
 
-    dt = torch.float32 if args.dtype == "f32" else torch.float64
-    e = 4 if args.dtype == "f32" else 8
+    dt = torch.float64 if args.dtype == "f64" else torch.float32
+    e = 8 if args.dtype == "f64" else 4
     m, n = args.m, args.n
     lay = gb.COL_MAJOR if args.layout == "col" else gb.ROW_MAJOR
 
@@ -51,6 +53,14 @@ def main(argv=None):
         ld = n if lay == gb.ROW_MAJOR else m
         call = lambda: gb.gemv(A, x, c, 1.0, lay, m, n, ld)
         nbytes = e * (m * n + n + 2 * m)
+    elif args.op == "gemvq":
+        A = torch.empty((m, n), dtype=torch.float32, device="cuda")
+        synth.fill_normal_rows(A, 0, 1, -3.0, 3.0)
+        x, c = filled(n, 2), filled(m, 3)
+        Q, sc = gb.quantize(A, args.dtype)
+        del A
+        call = lambda: gb.gemv_q(Q, sc, x, c, 1.0, n=n)
+        nbytes = (2 if args.dtype == "bf16" else 1) * m * n + 4 * n + 8 * m + (4 * m if sc is not None else 0)
     elif args.op == "dot":
         x, y, a = filled(n, 4), filled(n, 5), filled(1, 6)
         call = lambda: gb.dot(x, y, a, n)

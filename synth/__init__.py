@@ -25,6 +25,8 @@ Value maps (all exact in the target type):
 * uniform f64 in [-1, 1):  (u >> 11) * 2^-52 - 1
 * uniform f32 in [-1, 1):  (u >> 40) * 2^-23 - 1
 * integers in [lo, hi]:    lo + (((u >> 32) * (hi - lo + 1)) >> 32)
+* normal rows (device only): Box-Muller on words 2k+1, 2k+2 of element k,
+  times 10^(lo + (hi - lo) * u_i) per row, u_i from stream + 1
 """
 from __future__ import annotations
 
@@ -106,6 +108,10 @@ def _load():
             f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
                           ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
             f.restype = ctypes.c_int
+        f = lib.synth_normal_rows_f32
+        f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
+                      ctypes.c_uint64, ctypes.c_float, ctypes.c_float, ctypes.c_void_p]
+        f.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -137,6 +143,20 @@ def fill_integers(t, seed: int, stream: int, lo: int, hi: int, offset: int = 0) 
         rc = lib.synth_integers_f32(t.data_ptr(), t.numel(), seed, stream, offset, lo, hi, s)
     else:
         raise TypeError(t.dtype)
+    if rc != 0:
+        raise RuntimeError(f"synth fill failed: cuda error {rc}")
+
+
+def fill_normal_rows(t, seed: int, stream: int, lo: float = -3.0, hi: float = 3.0) -> None:
+    """Fill a contiguous row-major 2-D float32 CUDA tensor with N(0,1) values
+    (Box-Muller on two words per element) times a per-row scale
+    10^(lo + (hi - lo) * u_i), u_i uniform in [0, 1) from stream + 1 (the
+    reduced-precision GEMV workload: rows scaled log-uniformly)."""
+    import torch
+    assert t.is_cuda and t.is_contiguous() and t.dim() == 2 and t.dtype == torch.float32
+    lib = _load()
+    s = torch.cuda.current_stream(t.device).cuda_stream
+    rc = lib.synth_normal_rows_f32(t.data_ptr(), t.shape[0], t.shape[1], seed, stream, lo, hi, s)
     if rc != 0:
         raise RuntimeError(f"synth fill failed: cuda error {rc}")
 

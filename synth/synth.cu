@@ -52,6 +52,24 @@ __global__ void integers_kernel(T* out, int64_t n, uint64_t key, int64_t offset,
   }
 }
 
+// N(0,1) by Box-Muller (FP32) from the words 2k+1, 2k+2 of the stream, times a
+// row scale 10^(lo + (hi - lo) * u_i) with u_i the i-th word of stream + 1.
+__global__ void normal_rows_kernel(float* out, int64_t m, int64_t n, uint64_t key, uint64_t rkey,
+                                   float lo, float hi) {
+  const int64_t total = m * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n;
+    const uint64_t w1 = mix(key + (uint64_t)(2 * e + 1) * kG);
+    const uint64_t w2 = mix(key + (uint64_t)(2 * e + 2) * kG);
+    const float u1 = ((float)(uint32_t)(w1 >> 40) + 1.0f) * 0x1p-24f;  // (0, 1]
+    const float u2 = (float)(uint32_t)(w2 >> 40) * 0x1p-24f;           // [0, 1)
+    const float z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    const float ur = (float)(uint32_t)(mix(rkey + (uint64_t)(i + 1) * kG) >> 40) * 0x1p-24f;
+    out[e] = z * exp10f(lo + (hi - lo) * ur);
+  }
+}
+
 int grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -89,6 +107,14 @@ int synth_integers_f32(float* out, int64_t n, uint64_t seed, uint64_t stream, in
   if (n <= 0) return 0;
   integers_kernel<float><<<grid_for(n), 256, 0, (cudaStream_t)s>>>(
       out, n, key_of(seed, stream), offset, lo, (uint64_t)(hi - lo + 1));
+  return (int)cudaPeekAtLastError();
+}
+
+int synth_normal_rows_f32(float* out, int64_t m, int64_t n, uint64_t seed, uint64_t stream,
+                          float lo, float hi, void* s) {
+  if (m <= 0 || n <= 0) return 0;
+  normal_rows_kernel<<<grid_for(m * n), 256, 0, (cudaStream_t)s>>>(
+      out, m, n, key_of(seed, stream), key_of(seed, stream + 1), lo, hi);
   return (int)cudaPeekAtLastError();
 }
 
