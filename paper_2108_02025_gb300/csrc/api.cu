@@ -128,23 +128,25 @@ constexpr int64_t kWaveBlocks = 608;
 // else the most even S (units below one per block are penalised).  Chunks
 // hold at least `min_kc` indices (multiples of `quantum`); the partials'
 // traffic (16 bytes per row per chunk) stays under 1% of the matrix's.
-// Depends only on the shape.
-inline SplitShape block_split(int64_t items, int64_t n, int64_t min_kc, int64_t quantum, size_t e) {
+// `wave` is the number of blocks resident at once.  Depends only on the
+// shape.
+inline SplitShape block_split(int64_t items, int64_t n, int64_t min_kc, int64_t quantum, size_t e,
+                              int64_t wave = kWaveBlocks) {
   SplitShape s{1, 1, 1, n > 0 ? n : 1, items};
   int64_t smax = kMaxSplits;
   if (smax > n / min_kc) smax = n / min_kc;
   if (smax > n * (int64_t)e / 1600) smax = n * (int64_t)e / 1600;
   auto even = [&](int64_t S) {
-    const double u = (double)(items * S) / kWaveBlocks;  // units per block, average
-    const double busiest = (double)cdiv(items * S, kWaveBlocks);
+    const double u = (double)(items * S) / wave;  // units per block, average
+    const double busiest = (double)cdiv(items * S, wave);
     return (u / busiest) * (u < 1.0 ? u : 1.0);
   };
-  if (items >= 4 * kWaveBlocks || smax < 2) return s;
+  if (items >= 4 * wave || smax < 2) return s;
   int64_t best = 1;
   double best_even = even(1);
   for (int64_t S = 2; S <= smax; ++S) {
     const double ev = even(S);
-    if (items * S >= 4 * kWaveBlocks && ev >= 0.95) { best = S; break; }
+    if (items * S >= 4 * wave && ev >= 0.95) { best = S; break; }
     if (ev > best_even + 1e-9) { best = S; best_even = ev; }
   }
   if (best < 2) return s;
@@ -262,12 +264,13 @@ size_t dot_ws(size_t e, int64_t n) {
   return b;
 }
 
-// Reduced-precision GEMV (row-major): per-row counters, like the long-row
-// FP32 kernel; `per` elements per 16-byte pack.
+// Reduced-precision GEMV (row-major): items are groups of kQuantRows rows,
+// one counter per group; `per` elements per 16-byte pack.
 inline SplitShape qgemv_shape(int fmt, int64_t m, int64_t n) {
   const int64_t per = fmt == 0 ? 8 : 16;
   const int64_t quantum = 256 * per;
-  SplitShape s = block_split(m, n, quantum * kQuantU, quantum, 4);
+  SplitShape s = block_split(cdiv(m, kQuantRows[fmt]), n, quantum * kQuantPacks[fmt], quantum,
+                             fmt == 0 ? 2 : 1, 152 * kQuantMinBlocks[fmt]);
   s.G = s.S;
   s.NG = 1;
   return s;

@@ -25,7 +25,12 @@ struct GemvArgs {
 constexpr int kRowLongU = 4;     // packs in flight per thread, long-row kernel
 constexpr int kRowScalarRW = 4;  // rows per lane group, misaligned row-major kernel
 constexpr int kColTileU = 8;     // columns in flight per thread, column-major tile kernel
-constexpr int kQuantU = 2;       // 16-byte packs in flight per thread, BF16 / E4M3 GEMV
+// BF16 / E4M3 GEMV (index: 0 BF16, 1 E4M3): rows sharing each load of x,
+// 16-byte packs per row in flight per thread, and resident blocks per SM
+// the registers are budgeted for.
+constexpr int kQuantRows[2] = {4, 4};
+constexpr int kQuantPacks[2] = {2, 1};
+constexpr int kQuantMinBlocks[2] = {2, 3};
 
 // How one GEMV is cut into work.  The kernel, the split S and the per-thread
 // summation order depend only on (dtype, layout, m, n) and on the pointer

@@ -8,10 +8,11 @@
 //   s_i)); all-zero rows get s_i = 0 and codes 0.
 // * GEMV: c_i <- c_i + alpha * s_i * sum_j q_ij x_j (s_i = 1 for BF16), x
 //   and c FP32.  Row-major only, streamed like the FP32 long-row kernel (a
-//   block per (row, chunk) unit, consecutive units per block); products are
-//   FP32 fmas in chains of at most 32, folded into a compensated FP32 sum
+//   block per (row group, chunk) unit, consecutive units per block); products
+//   are FP32 fmas in chains of at most 32, folded into a compensated FP32 sum
 //   (TwoSum), then a fixed-order block sum.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
 #include "gb_common.cuh"
@@ -40,19 +41,6 @@ struct Fmt {
   static constexpr int PER = FMT == 0 ? 8 : 16;  // elements per 16-byte pack
   static constexpr int BYTES = FMT == 0 ? 2 : 1;
 };
-
-// Element k of a 16-byte pack held as 4 words.
-template <int FMT>
-__device__ __forceinline__ float unpack(const uint4& w, int k) {
-  const unsigned word = k < Fmt<FMT>::PER / 4 ? w.x : k < Fmt<FMT>::PER / 2 ? w.y : k < 3 * Fmt<FMT>::PER / 4 ? w.z : w.w;
-  if constexpr (FMT == 0) {
-    const int h = k & 1;
-    return bf16_bits_to_float(h ? word >> 16 : word & 0xFFFFu);
-  } else {
-    const int b = k & 3;
-    return e4m3_bits_to_float((word >> (8 * b)) & 0xFFu);
-  }
-}
 
 // ------------------------------------------------------------ quantisers ---
 
@@ -97,16 +85,53 @@ __global__ void __launch_bounds__(kThreads)
 
 // ------------------------------------------------------------------ GEMV ---
 
-// unit u = (row u / S, chunk u % S); block b takes units [b*U/G, (b+1)*U/G)
-template <int FMT, int U>
-__global__ void __launch_bounds__(kThreads, 4)
+// Four E4M3 codes (one word, element 0 in the low byte) -> FP32, exactly:
+// the conversion to a pair of binary16 values is exact (every E4M3 value,
+// subnormals included, is a binary16 normal) and so is the widening.
+__device__ __forceinline__ void e4m3x4_to_float(unsigned w, float& f0, float& f1, float& f2, float& f3) {
+  unsigned lo, hi;
+  asm("{\n .reg .b16 a, b;\n mov.b32 {a, b}, %2;\n cvt.rn.f16x2.e4m3x2 %0, a;\n cvt.rn.f16x2.e4m3x2 %1, b;\n}"
+      : "=r"(lo), "=r"(hi)
+      : "r"(w));
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+  f0 = a.x;
+  f1 = a.y;
+  f2 = b.x;
+  f3 = b.y;
+}
+
+// Elements 4k .. 4k+3 of a 16-byte pack.
+template <int FMT>
+__device__ __forceinline__ void unpack4(const uint4& w, int k, float& f0, float& f1, float& f2, float& f3) {
+  if constexpr (FMT == 0) {
+    const unsigned w0 = k == 0 ? w.x : w.z, w1 = k == 0 ? w.y : w.w;
+    f0 = __uint_as_float(w0 << 16);
+    f1 = __uint_as_float(w0 & 0xFFFF0000u);
+    f2 = __uint_as_float(w1 << 16);
+    f3 = __uint_as_float(w1 & 0xFFFF0000u);
+  } else {
+    e4m3x4_to_float(k == 0 ? w.x : k == 1 ? w.y : k == 2 ? w.z : w.w, f0, f1, f2, f3);
+  }
+}
+
+// Unit u = (row group u / S of R consecutive rows, chunk u % S of the
+// columns); block b takes units [b*U/G, (b+1)*U/G).  Each load of x serves
+// the R rows of the group: with one byte per element, reading x once per row
+// would cost four times the matrix's own traffic in L1.  A row's products
+// are FP32 fmas in chains of at most 32, folded into a compensated FP32 sum,
+// then a fixed-order block sum; a group's missing rows (past m) re-read row
+// m-1 and are dropped.
+template <int FMT, int R, int U, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
     gemv_q_kernel(int64_t m, int64_t n, float alpha, const unsigned char* __restrict__ Q,
                   int64_t ldq_bytes, const float* __restrict__ scales, const float* __restrict__ x,
                   float* __restrict__ c, const Split sp, int64_t KC, int64_t units) {
   constexpr int PER = Fmt<FMT>::PER;
-  constexpr int64_t STEP = (int64_t)kThreads * PER;      // columns per pack position
+  constexpr int EB = Fmt<FMT>::BYTES;
+  constexpr int64_t STEP = (int64_t)kThreads * PER;               // columns per pack position
   constexpr int CHAIN = 32 / (U * PER) > 0 ? 32 / (U * PER) : 1;  // bodies per FP32 chain
-  __shared__ float red[kThreads / 32];
+  __shared__ float red[R][kThreads / 32];
   __shared__ double red_d[kThreads / 32];
   __shared__ int flag;
 
@@ -114,77 +139,113 @@ __global__ void __launch_bounds__(kThreads, 4)
   const int64_t u0 = units * blockIdx.x / gridDim.x;
   const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
   for (int64_t u = u0; u < u1; ++u) {
-    const int64_t row = u / S;
-    const int s = (int)(u - row * S);
+    const int64_t g = u / S;
+    const int s = (int)(u - g * S);
+    const int64_t row0 = g * R;
     const int64_t k0 = (int64_t)s * KC;
     const int64_t k1 = (k0 + KC < n) ? k0 + KC : n;
     const int64_t kv1 = k0 + ((k1 - k0) / PER) * PER;
-    const unsigned char* Qr = Q + row * ldq_bytes;
+    const unsigned char* Qr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) Qr[r] = Q + (row0 + r < m ? row0 + r : m - 1) * ldq_bytes;
 
-    float acc = 0.f, hi = 0.f, lo = 0.f;
+    float acc[R], hi[R], lo[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = hi[r] = lo[r] = 0.f;
     int chain = 0;
     int64_t j = k0 + (int64_t)threadIdx.x * PER;
 #pragma unroll 1
     for (; j + (U - 1) * STEP < kv1; j += U * STEP) {
-      uint4 qp[U];
+      uint4 qp[U][R];
 #pragma unroll
       for (int q = 0; q < U; ++q)
-        qp[q] = __ldcs(reinterpret_cast<const uint4*>(Qr + (j + q * STEP) * Fmt<FMT>::BYTES));
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          qp[q][r] = __ldcs(reinterpret_cast<const uint4*>(Qr[r] + (j + q * STEP) * EB));
 #pragma unroll
       for (int q = 0; q < U; ++q) {
 #pragma unroll
-        for (int k4 = 0; k4 < PER; k4 += 4) {
-          const float4 xv = __ldg(reinterpret_cast<const float4*>(x + j + q * STEP + k4));
-          acc = __fmaf_rn(unpack<FMT>(qp[q], k4 + 0), xv.x, acc);
-          acc = __fmaf_rn(unpack<FMT>(qp[q], k4 + 1), xv.y, acc);
-          acc = __fmaf_rn(unpack<FMT>(qp[q], k4 + 2), xv.z, acc);
-          acc = __fmaf_rn(unpack<FMT>(qp[q], k4 + 3), xv.w, acc);
+        for (int k = 0; k < PER / 4; ++k) {
+          const float4 xv = __ldg(reinterpret_cast<const float4*>(x + j + q * STEP + 4 * k));
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            float f0, f1, f2, f3;
+            unpack4<FMT>(qp[q][r], k, f0, f1, f2, f3);
+            acc[r] = __fmaf_rn(f0, xv.x, acc[r]);
+            acc[r] = __fmaf_rn(f1, xv.y, acc[r]);
+            acc[r] = __fmaf_rn(f2, xv.z, acc[r]);
+            acc[r] = __fmaf_rn(f3, xv.w, acc[r]);
+          }
         }
       }
-      if (++chain == CHAIN) {  // fold the chain (at most 32 products) into (hi, lo)
+      if (++chain == CHAIN) {  // fold each row's chain (at most 32 products) into (hi, lo)
         chain = 0;
-        float e;
-        two_sum_f(hi, acc, hi, e);
-        lo = __fadd_rn(lo, e);
-        acc = 0.f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          float e;
+          two_sum_f(hi[r], acc[r], hi[r], e);
+          lo[r] = __fadd_rn(lo[r], e);
+          acc[r] = 0.f;
+        }
       }
     }
 #pragma unroll 1
     for (; j < kv1; j += STEP) {  // remaining whole packs, one at a time
-      const uint4 qv = __ldcs(reinterpret_cast<const uint4*>(Qr + j * Fmt<FMT>::BYTES));
-      float a2 = 0.f;
 #pragma unroll
-      for (int k = 0; k < PER; ++k) a2 = __fmaf_rn(unpack<FMT>(qv, k), __ldg(x + j + k), a2);
-      float e;
-      two_sum_f(hi, a2, hi, e);
-      lo = __fadd_rn(lo, e);
+      for (int r = 0; r < R; ++r) {
+        const uint4 qv = __ldcs(reinterpret_cast<const uint4*>(Qr[r] + j * EB));
+        float a2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < PER / 4; ++k) {
+          const float4 xv = __ldg(reinterpret_cast<const float4*>(x + j + 4 * k));
+          float f0, f1, f2, f3;
+          unpack4<FMT>(qv, k, f0, f1, f2, f3);
+          a2 = __fmaf_rn(f0, xv.x, a2);
+          a2 = __fmaf_rn(f1, xv.y, a2);
+          a2 = __fmaf_rn(f2, xv.z, a2);
+          a2 = __fmaf_rn(f3, xv.w, a2);
+        }
+        float e;
+        two_sum_f(hi[r], a2, hi[r], e);
+        lo[r] = __fadd_rn(lo[r], e);
+      }
     }
     if (kv1 + threadIdx.x < k1) {  // ragged end (< PER columns)
       const int64_t jj = kv1 + threadIdx.x;
-      const unsigned b = FMT == 0 ? (unsigned)reinterpret_cast<const uint16_t*>(Qr)[jj] : (unsigned)Qr[jj];
-      const float qv = FMT == 0 ? bf16_bits_to_float(b) : e4m3_bits_to_float(b);
-      acc = __fmaf_rn(qv, __ldg(x + jj), acc);
-    }
-    float v = hi + (lo + acc);
-
-    // fixed-order block sum (warp butterfly, then warps in order) in FP32
-    v = group_sum_f<32>(v);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float total = 0.f;
-    if (threadIdx.x == 0) {
+      const float xj = __ldg(x + jj);
 #pragma unroll
-      for (int w = 0; w < kThreads / 32; ++w) total = __fadd_rn(total, red[w]);
+      for (int r = 0; r < R; ++r) {
+        const float qv = FMT == 0 ? bf16_bits_to_float(reinterpret_cast<const uint16_t*>(Qr[r])[jj])
+                                  : e4m3_bits_to_float(Qr[r][jj]);
+        acc[r] = __fmaf_rn(qv, xj, acc[r]);
+      }
     }
-    const float sc = FMT == 1 ? scales[row] : 1.f;
+
+    // fixed-order block sums (warp butterfly, then warps in order) in FP32
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float v = group_sum_f<32>(hi[r] + (lo[r] + acc[r]));
+      if ((threadIdx.x & 31) == 0) red[r][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    const int64_t row = row0 + threadIdx.x;  // thread r < R finishes row row0 + r
+    const bool mine = threadIdx.x < R && row < m;
+    float total = 0.f;
+    if (mine) {
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) total = __fadd_rn(total, red[threadIdx.x][w]);
+    }
     if (S == 1) {
-      if (threadIdx.x == 0) c[row] = __fmaf_rn(alpha, __fmul_rn(sc, total), c[row]);
-    } else {
-      if (threadIdx.x == 0) sp.part[(int64_t)s * m + row] = (double)total;
-      if (arrive_last(sp.tickets + row, (unsigned)S, &flag)) {
+      if (mine) c[row] = __fmaf_rn(alpha, __fmul_rn(FMT == 1 ? scales[row] : 1.f, total), c[row]);
+      continue;
+    }
+    if (mine) sp.part[(int64_t)s * m + row] = (double)total;
+    if (arrive_last(sp.tickets + g, (unsigned)S, &flag)) {
+      for (int r = 0; r < R && row0 + r < m; ++r) {
+        const int64_t rr = row0 + r;
         double p = 0.0;
-        for (int q = threadIdx.x; q < S; q += kThreads) p = __dadd_rn(p, __ldcg(sp.part + (int64_t)q * m + row));
+        for (int q = threadIdx.x; q < S; q += kThreads) p = __dadd_rn(p, __ldcg(sp.part + (int64_t)q * m + rr));
         p = group_sum<32>(p);
         __syncthreads();
         if ((threadIdx.x & 31) == 0) red_d[threadIdx.x >> 5] = p;
@@ -193,10 +254,10 @@ __global__ void __launch_bounds__(kThreads, 4)
           double t = 0.0;
 #pragma unroll
           for (int w = 0; w < kThreads / 32; ++w) t = __dadd_rn(t, red_d[w]);
-          c[row] = __fmaf_rn(alpha, __fmul_rn(sc, (float)t), c[row]);
-          sp.tickets[row] = 0u;
+          c[rr] = __fmaf_rn(alpha, __fmul_rn(FMT == 1 ? scales[rr] : 1.f, (float)t), c[rr]);
         }
       }
+      if (threadIdx.x == 0) sp.tickets[g] = 0u;
     }
   }
 }
@@ -222,11 +283,11 @@ int gemv_q_launch(int fmt, int64_t m, int64_t n, float alpha, const void* Q, int
                   int64_t units, cudaStream_t st) {
   const unsigned char* q = static_cast<const unsigned char*>(Q);
   if (fmt == 0) {
-    auto kern = gemv_q_kernel<0, kQuantU>;
+    auto kern = gemv_q_kernel<0, kQuantRows[0], kQuantPacks[0], kQuantMinBlocks[0]>;
     const int grid = grid_size((const void*)kern, units);
     kern<<<grid, kThreads, 0, st>>>(m, n, alpha, q, ldq * 2, scales, x, c, sp, kc, units);
   } else {
-    auto kern = gemv_q_kernel<1, kQuantU>;
+    auto kern = gemv_q_kernel<1, kQuantRows[1], kQuantPacks[1], kQuantMinBlocks[1]>;
     const int grid = grid_size((const void*)kern, units);
     kern<<<grid, kThreads, 0, st>>>(m, n, alpha, q, ldq, scales, x, c, sp, kc, units);
   }
