@@ -405,6 +405,196 @@ def roofline_of(op, avg_s, hbm_gbs, src):
             "traffic": measured_traffic(name), "algorithmic_bytes": by}
 
 
+# ------------------------------------------------------- precision leg --
+
+PREC_N = 32768
+PREC_WORKLOAD = ("GEMV 32768x32768 row-major, A = N(0,1) with row i scaled by 10^U[-3,3] (FP32 "
+                 "master), stored as FP32 / BF16 / FP8-E4M3 with per-row FP32 scales; x uniform[-1,1] "
+                 "FP32; c FP32")
+PREC_BOUND = {"fp32": 2.0 ** -20, "bf16": 2.0 ** -9, "e4m3": 2.0 ** -4}
+
+
+def precision_bytes(form, m, n):
+    """Compulsory bytes of one reduced-precision GEMV: A's codes (and scales), x, c."""
+    a = {"fp32": 4, "bf16": 2, "e4m3": 1}[form] * m * n
+    return a + 4 * n + 8 * m + (4 * m if form == "e4m3" else 0)
+
+
+def run_precision(device, stream, reps=20, sample_rows=64):
+    """Solves/s of the 32768^2 GEMV with A stored as FP32 (plain method), BF16
+    and E4M3, timed with CUDA events (median of `reps` calls; A is larger
+    than L2), and the error of each form against an FP64 evaluation (numpy)
+    of the FP32 master on `sample_rows` seeded rows, relative to
+    sum_j |A_ij x_j|."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2108_02025_gb300 as gb
+    m = n = PREC_N
+    A = torch.empty((m, n), dtype=torch.float32, device=device)
+    synth.fill_normal_rows(A, 0, 201, -3.0, 3.0)
+    x = torch.empty(n, dtype=torch.float32, device=device)
+    synth.fill_uniform(x, 0, 203)
+    c = torch.zeros(m, dtype=torch.float32, device=device)
+    rows = np.unique(synth.integers(sample_rows, 0, 204, 0, m - 1, np.int64))
+    A_rows = A[torch.from_numpy(rows).to(device)].double().cpu().numpy()
+    xh = x.double().cpu().numpy()
+    want = A_rows @ xh
+    mag = np.abs(A_rows) @ np.abs(xh)
+    out = {"workload": PREC_WORKLOAD, "error": "max over sampled rows of |c_i - (A x)_i| / "
+           "sum_j |A_ij x_j|, FP64 numpy on the FP32 master", "sampled_rows": int(rows.size)}
+    forms = {}
+    for form in ("fp32", "bf16", "e4m3"):
+        if form == "fp32":
+            call = lambda: gb.gemv(A, x, c, 1.0, gb.ROW_MAJOR, stream=stream)
+        else:
+            Q, sc = gb.quantize(A, form, stream=stream)
+            call = lambda Q=Q, sc=sc: gb.gemv_q(Q, sc, x, c, 1.0, n=n, stream=stream)
+        c.zero_()
+        call()
+        got = c[torch.from_numpy(rows).to(device)].double().cpu().numpy()
+        err = float(np.max(np.abs(got - want) / mag))
+        for _ in range(3):
+            call()
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        t = statistics.median(times)
+        forms[form] = {"us": round(t * 1e6, 2), "solves_per_s": round(1.0 / t, 1),
+                       "GB_s": round(precision_bytes(form, m, n) / t / 1e9, 1),
+                       "max_rel_err": float(f"{err:.3e}"), "bound": PREC_BOUND[form]}
+        if form != "fp32":
+            del Q, sc
+    for form in ("bf16", "e4m3"):
+        forms[form]["speedup_vs_fp32"] = round(forms[form]["solves_per_s"] / forms["fp32"]["solves_per_s"], 3)
+    out["forms"] = forms
+    del A
+    torch.cuda.empty_cache()
+    return out
+
+
+# --------------------------------------------------------- batched leg --
+
+BATCH_COUNT = 4096
+BATCH_WORKLOAD = ("4096 independent FP32 GEMVs c += A x, m and n log-uniform in [32, 8192] "
+                  "(synth.log_uniform_integers, seed 0), row-major with lda = n rounded up to a "
+                  "multiple of 4, A, x, c uniform[-1,1]")
+
+
+class BatchWorkload:
+    """The batched-GEMV workload resident on the device: one arena each for
+    the A's, x's and c's, every operand 256-byte aligned."""
+
+    def __init__(self, device, count=BATCH_COUNT, seed=0, lo=32, hi=8192):
+        import numpy as np
+        import torch
+        import synth
+        self.m = synth.log_uniform_integers(count, seed, 301, lo, hi)
+        self.n = synth.log_uniform_integers(count, seed, 302, lo, hi)
+        self.lda = (self.n + 3) // 4 * 4
+
+        def offsets(sizes):
+            padded = (sizes + 63) // 64 * 64          # 256-byte aligned starts
+            off = np.concatenate([[0], np.cumsum(padded)[:-1]]).astype(np.int64)
+            return off, int(padded.sum())
+
+        self.a_off, na = offsets(self.m * self.lda)
+        self.x_off, nx = offsets(self.n)
+        self.c_off, nc = offsets(self.m)
+        self.A = torch.empty(max(na, 1), dtype=torch.float32, device=device)
+        self.x = torch.empty(max(nx, 1), dtype=torch.float32, device=device)
+        self.c = torch.empty(max(nc, 1), dtype=torch.float32, device=device)
+        synth.fill_uniform(self.A, seed, 303)
+        synth.fill_uniform(self.x, seed, 304)
+        synth.fill_uniform(self.c, seed, 305)
+        a0, x0, c0 = self.A.data_ptr(), self.x.data_ptr(), self.c.data_ptr()
+        self.problems = [(a0 + 4 * int(self.a_off[p]), x0 + 4 * int(self.x_off[p]),
+                          c0 + 4 * int(self.c_off[p]), 1.0, int(self.m[p]), int(self.n[p]),
+                          int(self.lda[p])) for p in range(count)]
+        self.bytes = int((4 * (self.m * self.n + self.n + 2 * self.m)).sum())
+        torch.cuda.synchronize(device)
+
+    def operands(self, p):
+        """(A as an m x lda view, x, c) of problem p."""
+        m, n, ld = int(self.m[p]), int(self.n[p]), int(self.lda[p])
+        a = self.A[self.a_off[p]:self.a_off[p] + m * ld].view(m, ld)
+        return a, self.x[self.x_off[p]:self.x_off[p] + n], self.c[self.c_off[p]:self.c_off[p] + m]
+
+
+def _time_events(fn, stream, reps):
+    import torch
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return statistics.median(times)
+
+
+def run_batched(device, stream, hbm, reps=5):
+    """The 4096 GEMVs as 4096 separate plain launches (gb_sgemv; host loop,
+    then the same calls captured in one CUDA graph) and as one persistent
+    batched launch (gb_sgemv_batch; direct, then replayed from a graph),
+    each timed with CUDA events on the launching stream (median of `reps`;
+    35 GB of operands, far above L2)."""
+    import torch
+    import paper_2108_02025_gb300 as gb
+    wl = BatchWorkload(device)
+    lib = gb.lib()
+    sh = stream.cuda_stream
+    nb = max(gb.gb_workspace_bytes(gb.OP_GEMV, gb.F32, gb.ROW_MAJOR, m, n) for
+             (_, _, _, _, m, n, _) in wl.problems)
+    ws = torch.zeros(max(nb, 1), dtype=torch.uint8, device=device)
+    wsp = ws.data_ptr()
+    f = lib.gb_sgemv
+
+    def separate(st):
+        for (a, x, c, al, m, n, ld) in wl.problems:
+            if f(0, m, n, al, a, ld, x, c, wsp, nb, st) != 0:
+                raise RuntimeError("gb_sgemv failed")
+
+    table = gb.load_tuning()
+    batch = gb.Batch(wl.problems, table=table, device=device)
+
+    def batched(st):
+        batch.launch(st)
+
+    out = {"workload": BATCH_WORKLOAD, "problems": len(wl.problems), "bytes": wl.bytes,
+           "tiles": batch.tiles,
+           "tuning": "autotuned table" if os.path.exists(gb.TUNING_PATH) else "built-in table"}
+    cap = torch.cuda.Stream(device)  # graphs are captured on a side stream
+    for name, fn in (("separate", separate), ("batched", batched)):
+        fn(sh)
+        torch.cuda.synchronize(device)
+        t = _time_events(lambda: fn(sh), stream, reps)
+        g = torch.cuda.CUDAGraph()
+        cap.wait_stream(stream)
+        with torch.cuda.graph(g, stream=cap):
+            fn(cap.cuda_stream)
+        stream.wait_stream(cap)
+        g.replay()
+        torch.cuda.synchronize(device)
+        tg = _time_events(g.replay, stream, reps)
+        del g
+        for key, tt in ((name, t), (name + "_graph", tg)):
+            out[key] = {"ms": round(tt * 1e3, 3), "GB_s": round(wl.bytes / tt / 1e9, 1),
+                        "frac_hbm": round(wl.bytes / tt / 1e9 / hbm, 4),
+                        "solves_per_s": round(len(wl.problems) / tt, 1),
+                        "launches": 1 if name == "batched" else len(wl.problems)}
+    out["speedup_vs_separate"] = round(out["separate"]["ms"] / out["batched_graph"]["ms"], 3)
+    del batch, wl, ws
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------- arms --
 
 def run_ours(args):
@@ -468,6 +658,11 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(wl, stream, device, bytes_step, args, world)
 
+    precision = batched = None
+    if not args.no_growth:
+        precision = run_precision(device, stream)
+        batched = run_batched(device, stream, hbm)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
@@ -499,6 +694,8 @@ def run_ours(args):
             "gpu_launches": len(ops) * args.steps,
             "clocks": clocks.summary(wall0, wall1),
             "ops": ops_report,
+            "precision": precision,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -589,6 +786,8 @@ def main(argv=None):
     p.add_argument("--e2e-steps", type=int, default=5, help="steps of the host-buffer (e2e) leg")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    p.add_argument("--no-growth", action="store_true",
+                   help="skip the reduced-precision, batched and serving legs")
     args = p.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         p.error("--warmup must be at least 3")

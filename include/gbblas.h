@@ -207,6 +207,72 @@ int gb_gemv_e4m3(int64_t m, int64_t n, float alpha, const uint8_t *Q, int64_t ld
                  const float *scales, const float *x, float *c, void *ws, size_t ws_bytes,
                  gb_stream stream);
 
+/* Batched FP32 GEMV: `count` independent row-major problems
+       c_p <- c_p + alpha_p * A_p x_p     (Def. GEMV, Sec. 3.1; m_p x n_p, lda_p)
+   in ONE persistent kernel launch.  Not an operation of the paper: it is the
+   GPU answer to the thread overhead that the paper finds dominating small
+   problems (Sec. 4.1, speedup bound; Sec. 4.2, Analysis), here a launch per
+   small GEMV.
+
+   Plan, then launch.  gb_sgemv_batch_plan (host only, no CUDA call) writes
+   the problems and their tiles into a caller-owned HOST buffer of
+   gb_sgemv_batch_plan_bytes() bytes, 16-byte aligned.  The caller copies
+   those bytes unchanged into DEVICE memory (16-byte aligned) and passes both
+   copies to gb_sgemv_batch, which enqueues one kernel that reads only the
+   device copy: the launch can be captured in a CUDA graph and replayed for
+   as long as the operands stay where the plan says.  Problems with m, n or
+   alpha zero are skipped (c untouched).  No c may overlap another problem's
+   c, or any A or x of the batch.
+
+   Tiling and tuning.  A problem's rows are cut into tiles of whole rows of
+   about `tile_bytes` bytes of A (a multiple of the block's 256 / lanes_per_row
+   row groups); each block of the launch processes the tiles whose cost
+   falls in its equal share of the batch's total.  In a tile, groups of
+   `lanes_per_row` lanes sum one row each, `packs_per_iter` 16-byte packs of
+   A per lane in flight; every lane forms FP32 fma chains of at most 64
+   products folded into a compensated FP32 sum (TwoSum), and the group adds
+   its lanes by a fixed butterfly.  The parameters come from a table of
+   GB_BATCH_BUCKETS entries indexed by the bucket ceil(log2(n_p)) (n_p = 1:
+   bucket 0); NULL selects the built-in table.  A row's result depends only
+   on n_p and its bucket's entry: under the same table a problem gives
+   bit-identical results alone or in any batch.  Problems whose A or x is not
+   16-byte aligned, or whose lda is not a multiple of 4, take a scalar path
+   in the same launch. */
+#define GB_BATCH_BUCKETS 32
+typedef struct {
+  int32_t lanes_per_row;  /* 1, 2, 4, 8, 16 or 32 */
+  int32_t packs_per_iter; /* 1, 2 or 4 */
+  int32_t tile_bytes;     /* target bytes of A per tile, >= 4096 */
+  int32_t reserved;       /* 0 */
+} gb_batch_tuning;
+
+/* The built-in table (GB_BATCH_BUCKETS entries written to `table`). */
+void gb_sgemv_batch_default_tuning(gb_batch_tuning *table);
+
+/* Bytes of the plan of a batch (a pure function of count, m, n, alpha and
+   the table); 0 when count < 0, m or n is NULL with count > 0, some m_p or
+   n_p is negative or above INT32_MAX, or the table has an invalid entry. */
+size_t gb_sgemv_batch_plan_bytes(int64_t count, const int64_t *m, const int64_t *n,
+                                 const float *alpha, const gb_batch_tuning *table);
+
+/* Build the plan.  Host arrays of `count` entries: m (2), n (3), lda (4,
+   >= max(1, n_p)), alpha (5), and DEVICE pointers A (6), x (7), c (8);
+   table (9, NULL = built-in); plan (10), plan_bytes (11).  Returns GB_OK or
+   -k for the first invalid argument k (including overlaps, reported on c,
+   and m_p, n_p above INT32_MAX). */
+int gb_sgemv_batch_plan(int64_t count, const int64_t *m, const int64_t *n, const int64_t *lda,
+                        const float *alpha, const float *const *A, const float *const *x,
+                        float *const *c, const gb_batch_tuning *table, void *plan,
+                        size_t plan_bytes);
+
+/* Enqueue the batch on `stream`: one launch.  plan_host (1) is the host
+   plan (read for the launch size), plan_dev (2) its device copy.  Returns
+   GB_OK, -1 (not a plan), -2 (plan_dev NULL or misaligned) or GB_ERR_CUDA. */
+int gb_sgemv_batch(const void *plan_host, const void *plan_dev, gb_stream stream);
+
+/* Number of tiles in a host plan (-1 if it is not a plan). */
+int64_t gb_sgemv_batch_tiles(const void *plan_host);
+
 /* GEMV without allocation.  The paper has no counterpart: this entry point
    exists for callers that cannot allocate device memory (code running where
    cudaMalloc is not allowed, such as a host callback, or a runtime that owns

@@ -61,9 +61,16 @@ def _load() -> ctypes.CDLL:
     lib.gb_quantize_e4m3.argtypes = [I64, I64, P, I64, P, I64, P, P]
     lib.gb_gemv_bf16.argtypes = [I64, I64, F, P, I64, P, P, P, SZ, P]
     lib.gb_gemv_e4m3.argtypes = [I64, I64, F, P, I64, P, P, P, P, SZ, P]
+    lib.gb_sgemv_batch_default_tuning.argtypes = [P]
+    lib.gb_sgemv_batch_default_tuning.restype = None
+    lib.gb_sgemv_batch_plan_bytes.argtypes = [I64, P, P, P, P]
+    lib.gb_sgemv_batch_plan_bytes.restype = SZ
+    lib.gb_sgemv_batch_plan.argtypes = [I64, P, P, P, P, P, P, P, P, P, SZ]
+    lib.gb_sgemv_batch.argtypes = [P, P, P]
+    lib.gb_sgemv_batch_tiles.argtypes, lib.gb_sgemv_batch_tiles.restype = [P], I64
     for name in ("gb_dgemv", "gb_sgemv", "gb_ddot", "gb_sdot", "gb_dger", "gb_sger",
                  "gb_dgemv_noalloc", "gb_quantize_bf16", "gb_quantize_e4m3", "gb_gemv_bf16",
-                 "gb_gemv_e4m3"):
+                 "gb_gemv_e4m3", "gb_sgemv_batch_plan", "gb_sgemv_batch"):
         getattr(lib, name).restype = I
     return lib
 
@@ -74,7 +81,8 @@ _lib = _load()
 EXPORTS = ("gb_version", "gb_status_string", "gb_workspace_bytes", "gb_workspace_init",
            "gb_dgemv", "gb_sgemv", "gb_ddot", "gb_sdot", "gb_dger", "gb_sger",
            "gb_dgemv_noalloc", "gb_quantize_bf16", "gb_quantize_e4m3", "gb_gemv_bf16",
-           "gb_gemv_e4m3")
+           "gb_gemv_e4m3", "gb_sgemv_batch_default_tuning", "gb_sgemv_batch_plan_bytes",
+           "gb_sgemv_batch_plan", "gb_sgemv_batch", "gb_sgemv_batch_tiles")
 
 
 def lib() -> ctypes.CDLL:
@@ -168,6 +176,138 @@ def gb_dgemv_noalloc(layout, m, n, alpha, A, lda, x, c, stream=None) -> int:
     for callers that cannot allocate device memory."""
     return _lib.gb_dgemv_noalloc(layout, m, n, alpha, _ptr(A), lda, _ptr(x), _ptr(c),
                                  _stream(stream))
+
+
+# ------------------------------------------------------- batched GEMV ----
+
+BATCH_BUCKETS = 32
+
+
+class BatchTuning(ctypes.Structure):
+    """One entry of the batched GEMV tuning table (gb_batch_tuning)."""
+    _fields_ = [("lanes_per_row", ctypes.c_int32), ("packs_per_iter", ctypes.c_int32),
+                ("tile_bytes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+TuningTable = BatchTuning * BATCH_BUCKETS
+
+
+def _addr(buf) -> int | None:
+    """Address of a ctypes object, a numpy array or an int (None = NULL)."""
+    if buf is None or isinstance(buf, int):
+        return buf
+    if hasattr(buf, "ctypes"):
+        return buf.ctypes.data
+    return ctypes.addressof(buf)
+
+
+def gb_sgemv_batch_default_tuning(table) -> None:
+    _lib.gb_sgemv_batch_default_tuning(_addr(table))
+
+
+def gb_sgemv_batch_plan_bytes(count, m, n, alpha, table=None) -> int:
+    """m, n: int64 host arrays; alpha: float32 host array (numpy or addresses)."""
+    return _lib.gb_sgemv_batch_plan_bytes(count, _addr(m), _addr(n), _addr(alpha), _addr(table))
+
+
+def gb_sgemv_batch_plan(count, m, n, lda, alpha, A, x, c, table, plan, plan_bytes) -> int:
+    """m, n, lda int64, alpha float32, A/x/c uint64 (device addresses): host
+    arrays; plan: host buffer (numpy uint8 array or address)."""
+    return _lib.gb_sgemv_batch_plan(count, _addr(m), _addr(n), _addr(lda), _addr(alpha), _addr(A),
+                                    _addr(x), _addr(c), _addr(table), _addr(plan), plan_bytes)
+
+
+def gb_sgemv_batch(plan_host, plan_dev, stream=None) -> int:
+    return _lib.gb_sgemv_batch(_addr(plan_host), _ptr(plan_dev), _stream(stream))
+
+
+def gb_sgemv_batch_tiles(plan_host) -> int:
+    return _lib.gb_sgemv_batch_tiles(_addr(plan_host))
+
+
+def tuning_table(entries=None):
+    """A ctypes tuning table: the built-in one, overridden bucket by bucket by
+    ``entries`` ({bucket: (lanes_per_row, packs_per_iter, tile_bytes)})."""
+    t = TuningTable()
+    gb_sgemv_batch_default_tuning(t)
+    for b, (lpr, u, tb) in (entries or {}).items():
+        t[int(b)] = BatchTuning(int(lpr), int(u), int(tb), 0)
+    return t
+
+
+TUNING_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "batch_tuning.json")
+
+
+def load_tuning(path: str | None = None):
+    """The table written by the autotuner (``batch_tuning.json`` beside this
+    file), or the built-in table when there is none."""
+    import json
+    path = TUNING_PATH if path is None else path
+    if not os.path.exists(path):
+        return tuning_table()
+    with open(path) as f:
+        d = json.load(f)
+    return tuning_table({int(b): tuple(v) for b, v in d["buckets"].items()})
+
+
+class Batch:
+    """A planned batch of FP32 row-major GEMVs c_p += alpha_p A_p x_p, run by
+    one persistent launch (``launch``) or by replaying a captured CUDA graph
+    of that launch (``capture`` then ``replay``).  ``problems`` is a list of
+    (A, x, c, alpha) with A a 2-D CUDA tensor (unit column stride) or
+    (A, x, c, alpha, m, n, lda) with A any tensor or device address."""
+
+    def __init__(self, problems, table=None, device=None):
+        import numpy as np
+        import torch
+        count = len(problems)
+        m = np.zeros(count, np.int64)
+        n = np.zeros(count, np.int64)
+        lda = np.zeros(count, np.int64)
+        alpha = np.zeros(count, np.float32)
+        A = np.zeros(count, np.uint64)
+        x = np.zeros(count, np.uint64)
+        c = np.zeros(count, np.uint64)
+        for i, pr in enumerate(problems):
+            if len(pr) == 4:
+                a, xv, cv, al = pr
+                mi, ni = a.shape
+                ld = a.stride(0) if mi > 1 else max(1, ni)
+            else:
+                a, xv, cv, al, mi, ni, ld = pr
+            m[i], n[i], lda[i], alpha[i] = mi, ni, ld, al
+            A[i], x[i], c[i] = _ptr(a) or 0, _ptr(xv) or 0, _ptr(cv) or 0
+        self.table = tuning_table() if table is None else table
+        nb = gb_sgemv_batch_plan_bytes(count, m, n, alpha, self.table)
+        if nb == 0:
+            raise GbError(-1, "sgemv_batch_plan_bytes")
+        self.host = np.zeros(nb + 16, np.uint8)
+        off = (-self.host.ctypes.data) % 16
+        self.host = self.host[off:off + nb]
+        _check(gb_sgemv_batch_plan(count, m, n, lda, alpha, A, x, c, self.table, self.host, nb),
+               "sgemv_batch_plan")
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.dev = torch.from_numpy(self.host.copy()).to(dev)
+        torch.cuda.synchronize(dev)
+        self.tiles = gb_sgemv_batch_tiles(self.host)
+        self.count = count
+        self.graph = None
+
+    def launch(self, stream=None) -> None:
+        _check(gb_sgemv_batch(self.host, self.dev, stream), "sgemv_batch")
+
+    def capture(self, stream=None) -> None:
+        """Capture one launch into a CUDA graph (torch.cuda.CUDAGraph)."""
+        import torch
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(self.dev.device) if stream is None else stream
+        s.wait_stream(torch.cuda.current_stream(self.dev.device))
+        with torch.cuda.graph(g, stream=s):
+            self.launch(torch.cuda.current_stream(self.dev.device))
+        self.graph = g
+
+    def replay(self) -> None:
+        self.graph.replay()
 
 
 # ---------------------------------------------------------- convenience ----

@@ -92,6 +92,14 @@ def integers(n: int, seed: int, stream: int, lo: int, hi: int, dtype=np.float64,
 _lib = None
 
 
+def log_uniform_integers(n: int, seed: int, stream: int, lo: int, hi: int) -> np.ndarray:
+    """round(exp(ln lo + u (ln hi - ln lo))) with u uniform in [0, 1): sizes
+    spread evenly over the decades between lo and hi (int64)."""
+    u = (uniform(n, seed, stream) + 1.0) * 0.5
+    v = np.round(np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo))))
+    return np.clip(v, lo, hi).astype(np.int64)
+
+
 def _load():
     global _lib
     if _lib is None:

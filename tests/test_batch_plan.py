@@ -1,0 +1,231 @@
+"""Host planner of the batched FP32 GEMV (gb_sgemv_batch_plan): a pure host
+function of the C ABI, so it is tested here without a GPU.  Device pointers
+are fake addresses: the planner stores them and checks overlaps, it never
+dereferences them.
+
+Checked: every row of every active problem lies in exactly one tile, the
+tiles of a problem are consecutive and ordered, a tile holds a multiple of
+the block's row groups (except a problem's last), the cost prefix is
+increasing and ends at the total, the tuning entry is the one of the
+problem's bucket ceil(log2 n), the plan of a problem is the same alone and
+in a mix, and the argument checks."""
+import numpy as np
+import pytest
+
+import paper_2108_02025_gb300 as gb
+import synth
+
+HEADER = np.dtype([("magic", "<u4"), ("version", "<u4"), ("count", "<i8"), ("tiles", "<i8"),
+                   ("total", "<i8"), ("off_problems", "<i8"), ("off_tiles", "<i8"),
+                   ("off_prefix", "<i8"), ("reserved", "<i8")])
+PROBLEM = np.dtype([("A", "<u8"), ("x", "<u8"), ("c", "<u8"), ("lda", "<i8"), ("m", "<i4"),
+                    ("n", "<i4"), ("alpha", "<f4"), ("vec", "<i4")])
+TILE = np.dtype([("p", "<i4"), ("row0", "<i4"), ("rows", "<i4"), ("lpr_log2", "u1"),
+                 ("u_log2", "u1"), ("pad", "<u2")])
+
+
+def log_uniform(count, seed, stream, lo, hi):
+    u = (synth.uniform(count, seed, stream) + 1.0) / 2.0
+    return np.round(np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))).astype(np.int64)
+
+
+class FakeBatch:
+    """Problems laid out at fake, disjoint, 256-byte aligned addresses."""
+
+    def __init__(self, m, n, alpha=None, pad=3, base=1 << 40):
+        self.count = len(m)
+        self.m = np.asarray(m, np.int64)
+        self.n = np.asarray(n, np.int64)
+        self.lda = np.maximum(self.n + pad, 1).astype(np.int64)
+        self.alpha = np.ones(self.count, np.float32) if alpha is None else np.asarray(alpha, np.float32)
+        self.A = np.zeros(self.count, np.uint64)
+        self.x = np.zeros(self.count, np.uint64)
+        self.c = np.zeros(self.count, np.uint64)
+        addr = base
+        for p in range(self.count):
+            for name, nbytes in (("A", 4 * int(self.m[p]) * int(self.lda[p])), ("x", 4 * int(self.n[p])),
+                                 ("c", 4 * int(self.m[p]))):
+                getattr(self, name)[p] = addr
+                addr += (nbytes + 255) // 256 * 256 + 256
+
+    def plan(self, table=None):
+        nb = gb.gb_sgemv_batch_plan_bytes(self.count, self.m, self.n, self.alpha, table)
+        assert nb > 0
+        buf = aligned_buffer(nb)
+        st = gb.gb_sgemv_batch_plan(self.count, self.m, self.n, self.lda, self.alpha, self.A, self.x,
+                                    self.c, table, buf, nb)
+        return st, buf
+
+    def call(self, table=None, plan=None, nbytes=None, **override):
+        args = {k: getattr(self, k) for k in ("m", "n", "lda", "alpha", "A", "x", "c")}
+        args.update(override)
+        if plan is None:
+            nbytes = 1 << 20
+            plan = aligned_buffer(nbytes)
+        return gb.gb_sgemv_batch_plan(self.count, args["m"], args["n"], args["lda"], args["alpha"],
+                                      args["A"], args["x"], args["c"], table, plan, nbytes)
+
+
+def aligned_buffer(nbytes):
+    raw = np.zeros(nbytes + 16, np.uint8)
+    off = (-raw.ctypes.data) % 16
+    return raw[off:off + nbytes]
+
+
+def decode(buf):
+    h = np.frombuffer(buf[:HEADER.itemsize].tobytes(), HEADER)[0]
+    probs = np.frombuffer(buf[h["off_problems"]:h["off_problems"] + h["count"] * PROBLEM.itemsize].tobytes(),
+                          PROBLEM)
+    tiles = np.frombuffer(buf[h["off_tiles"]:h["off_tiles"] + h["tiles"] * TILE.itemsize].tobytes(), TILE)
+    prefix = np.frombuffer(buf[h["off_prefix"]:h["off_prefix"] + (h["tiles"] + 1) * 8].tobytes(), "<i8")
+    return h, probs, tiles, prefix
+
+
+def bucket(n):
+    b = 0
+    while b < gb.BATCH_BUCKETS - 1 and (1 << b) < n:
+        b += 1
+    return b
+
+
+def check_plan(fb, buf, table):
+    h, probs, tiles, prefix = decode(buf)
+    assert h["magic"] == 0x47425042 and h["count"] == fb.count
+    assert h["tiles"] == gb.gb_sgemv_batch_tiles(buf)
+    assert prefix[0] == 0 and prefix[-1] == h["total"]
+    assert np.all(np.diff(prefix) > 0)
+    for p in range(fb.count):
+        pr = probs[p]
+        assert (pr["m"], pr["n"], pr["lda"]) == (fb.m[p], fb.n[p], fb.lda[p])
+        assert (pr["A"], pr["x"], pr["c"]) == (fb.A[p], fb.x[p], fb.c[p])
+        mine = tiles[tiles["p"] == p]
+        idx = np.nonzero(tiles["p"] == p)[0]
+        active = fb.m[p] > 0 and fb.n[p] > 0 and fb.alpha[p] != 0
+        if not active:
+            assert mine.size == 0
+            continue
+        assert np.all(np.diff(idx) == 1), "tiles of a problem are consecutive"
+        starts = np.concatenate([[0], np.cumsum(mine["rows"])[:-1]])
+        assert np.array_equal(mine["row0"], starts) and mine["rows"].sum() == fb.m[p]
+        e = table[bucket(int(fb.n[p]))]
+        assert np.all(mine["lpr_log2"] == int(np.log2(e.lanes_per_row)))
+        assert np.all(mine["u_log2"] == int(np.log2(e.packs_per_iter)))
+        groups = 256 // e.lanes_per_row
+        assert np.all(mine["rows"][:-1] % groups == 0) and np.all(mine["rows"] > 0)
+        assert np.all(mine["rows"][:-1] == mine["rows"][0])
+    return h, probs, tiles, prefix
+
+
+def test_default_table():
+    t = gb.tuning_table()
+    for b in range(gb.BATCH_BUCKETS):
+        e = t[b]
+        assert e.lanes_per_row in (1, 2, 4, 8, 16, 32)
+        assert e.packs_per_iter in (1, 2, 4)
+        assert e.tile_bytes >= 4096 and e.reserved == 0
+    assert t[13].lanes_per_row == 32  # n up to 8192: 2048 packs per row
+
+
+def test_buckets():
+    assert [bucket(n) for n in (1, 2, 3, 32, 33, 64, 8192, 8193)] == [0, 1, 2, 5, 6, 6, 13, 14]
+
+
+def test_random_batch_covers_every_row():
+    count = 300
+    m = log_uniform(count, 0, 1, 32, 8192)
+    n = log_uniform(count, 0, 2, 32, 8192)
+    fb = FakeBatch(m, n)
+    table = gb.tuning_table()
+    st, buf = fb.plan(table)
+    assert st == gb.GB_OK
+    h, probs, tiles, prefix = check_plan(fb, buf, table)
+    # cost per tile: rows * (4n + 8) + 4n + 256
+    pn = probs["n"][tiles["p"]].astype(np.int64)
+    cost = tiles["rows"].astype(np.int64) * (4 * pn + 8) + 4 * pn + 256
+    assert np.array_equal(np.diff(prefix), cost)
+    # aligned fake addresses and lda = n + 3: only n = 1 (mod 4) rows are 16-byte multiples
+    assert np.array_equal(probs["vec"].astype(bool), (fb.lda % 4) == 0)
+
+
+def test_null_table_is_default_and_custom_table_is_used():
+    fb = FakeBatch([100, 5000, 7], [40, 3000, 9000])
+    st, buf = fb.plan(None)
+    assert st == gb.GB_OK
+    check_plan(fb, buf, gb.tuning_table())
+    custom = gb.tuning_table({b: (4, 1, 8192) for b in range(gb.BATCH_BUCKETS)})
+    st, buf = fb.plan(custom)
+    assert st == gb.GB_OK
+    h, probs, tiles, prefix = check_plan(fb, buf, custom)
+    assert np.all(tiles["lpr_log2"] == 2) and np.all(tiles["u_log2"] == 0)
+
+
+def test_inactive_problems_have_no_tiles_and_may_be_null():
+    fb = FakeBatch([0, 50, 60, 70], [10, 0, 20, 30], alpha=[1, 1, 0, 2])
+    for name in ("A", "x", "c"):
+        getattr(fb, name)[:3] = 0
+    st, buf = fb.plan(gb.tuning_table())
+    assert st == gb.GB_OK
+    h, probs, tiles, prefix = check_plan(fb, buf, gb.tuning_table())
+    assert set(tiles["p"].tolist()) == {3}
+
+
+def test_empty_batch():
+    fb = FakeBatch([], [])
+    st, buf = fb.plan(None)
+    assert st == gb.GB_OK
+    h, _, tiles, prefix = decode(buf)
+    assert h["tiles"] == 0 and prefix.tolist() == [0]
+
+
+def test_same_problem_same_tiles_alone_and_in_a_mix():
+    m = log_uniform(50, 3, 1, 32, 8192)
+    n = log_uniform(50, 3, 2, 32, 8192)
+    mix = FakeBatch(m, n)
+    _, buf = mix.plan(None)
+    _, _, tiles_mix, _ = decode(buf)
+    for p in (0, 17, 49):
+        alone = FakeBatch(m[p:p + 1], n[p:p + 1])
+        _, b1 = alone.plan(None)
+        _, _, t1, _ = decode(b1)
+        tm = tiles_mix[tiles_mix["p"] == p]
+        for f in ("row0", "rows", "lpr_log2", "u_log2"):
+            assert np.array_equal(t1[f], tm[f])
+
+
+def test_argument_checks():
+    fb = FakeBatch([10, 20], [30, 40])
+    assert fb.call(m=np.array([10, -1], np.int64)) == -2
+    assert fb.call(n=np.array([-5, 40], np.int64)) == -3
+    assert fb.call(m=np.array([10, 2 ** 31], np.int64)) == -2
+    assert fb.call(lda=np.array([29, 43], np.int64)) == -4
+    assert fb.call(A=np.array([0, fb.A[1]], np.uint64)) == -6
+    assert fb.call(x=np.array([fb.x[0], 0], np.uint64)) == -7
+    assert fb.call(c=np.array([0, fb.c[1]], np.uint64)) == -8
+    # c of problem 1 overlapping c of problem 0, then A of problem 0
+    assert fb.call(c=np.array([fb.c[0], fb.c[0] + 8], np.uint64)) == -8
+    assert fb.call(c=np.array([fb.c[0], fb.A[0] + 4 * 50], np.uint64)) == -8
+    # c of problem 0 overlapping its own x
+    assert fb.call(c=np.array([fb.x[0], fb.c[1]], np.uint64)) == -8
+    bad = gb.tuning_table({7: (3, 1, 65536)})
+    assert fb.call(table=bad) == -9
+    assert gb.gb_sgemv_batch_plan_bytes(2, fb.m, fb.n, fb.alpha, bad) == 0
+    assert fb.call(table=gb.tuning_table({7: (4, 8, 65536)})) == -9
+    assert fb.call(table=gb.tuning_table({7: (4, 1, 100)})) == -9
+    nb = gb.gb_sgemv_batch_plan_bytes(2, fb.m, fb.n, fb.alpha, None)
+    buf = aligned_buffer(nb + 16)
+    assert fb.call(plan=buf[1:], nbytes=nb) == -10
+    assert fb.call(plan=buf, nbytes=nb - 16) == -11
+    assert fb.call(plan=buf, nbytes=nb) == gb.GB_OK
+    assert gb.gb_sgemv_batch_plan(-1, None, None, None, None, None, None, None, None, buf, nb) == -1
+    assert gb.gb_sgemv_batch_plan_bytes(-1, None, None, None, None) == 0
+
+
+def test_launch_rejects_a_non_plan_without_touching_the_device():
+    junk = aligned_buffer(64)
+    assert gb.gb_sgemv_batch(junk, 1 << 40, 0) == -1
+    assert gb.gb_sgemv_batch_tiles(junk) == -1
+    fb = FakeBatch([10], [30])
+    st, buf = fb.plan(None)
+    assert st == gb.GB_OK
+    assert gb.gb_sgemv_batch(buf, None, 0) == -2
+    assert gb.gb_sgemv_batch(buf, (1 << 40) + 4, 0) == -2

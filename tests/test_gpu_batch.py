@@ -1,0 +1,157 @@
+"""Batched FP32 GEMV (gb_sgemv_batch: many row-major problems, one
+persistent launch) on the GPU against the CPU oracle, problem by problem,
+element by element (Def. GEMV per problem).
+
+Tolerance as for the single FP32 GEMV, per row i of problem p:
+    |c_i - c_oracle_i| / (|c0_i| + |alpha_p| sum_j |A_ij x_j|) <= 1e-5
+Also: a problem's result is bit-identical alone and in any batch, a graph
+replay equals a direct launch, every kernel variant a tuning table can
+select passes, padding (NaN) and bytes around every c are never touched,
+and the full-size workload (4096 problems, m, n log-uniform in [32, 8192])
+matches the oracle on sampled problems."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2108_02025_gb300 as gb
+import synth
+from gpu_util import Guarded, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def make(m, n, pad, seed):
+    ld = max(n + pad, 1)
+    size = (m - 1) * ld + n if m > 0 and n > 0 else 0
+    A = synth.uniform(size, seed, 1, np.float32)
+    for r in range(m - 1):
+        A[r * ld + n:(r + 1) * ld] = np.nan  # any read of padding poisons c
+    x = synth.uniform(n, seed, 2, np.float32)
+    c0 = synth.uniform(m, seed, 3, np.float32)
+    return A, x, c0, ld
+
+
+class Problem:
+    def __init__(self, m, n, pad=0, alpha=0.75, seed=0, misalign=0):
+        self.m, self.n, self.alpha, self.misalign = m, n, alpha, misalign
+        self.A, self.x, self.c0, self.ld = make(m, n, pad, seed)
+
+    def device(self):
+        self.dA = to_dev(self.A, self.misalign)
+        self.dx = to_dev(self.x, self.misalign)
+        self.dc = Guarded(self.c0, self.misalign)
+        return (self.dA, self.dx, self.dc.view, self.alpha, self.m, self.n, self.ld)
+
+    def want(self):
+        return (oracle.gemv(0, self.m, self.n, self.alpha, self.A, self.ld, self.x, self.c0),
+                oracle.gemv_scale(0, self.m, self.n, self.alpha, self.A, self.ld, self.x, self.c0))
+
+
+def run(problems, table=None, graph=False, launches=1):
+    b = gb.Batch([p.device() for p in problems], table=table)
+    if graph:
+        b.capture()
+        for _ in range(launches):
+            b.replay()
+    else:
+        for _ in range(launches):
+            b.launch()
+    torch.cuda.synchronize()
+    return [p.dc.result() for p in problems], b
+
+
+def mixed(seed=0, count=60):
+    ms = synth.log_uniform_integers(count, seed, 11, 1, 3000)
+    ns = synth.log_uniform_integers(count, seed, 12, 1, 3000)
+    pads = synth.integers(count, seed, 13, 0, 5, np.int64)
+    mis = synth.integers(count, seed, 14, 0, 3, np.int64)
+    probs = [Problem(int(ms[i]), int(ns[i]), int(pads[i]), 0.75 if i % 3 else -1.25, seed * 1000 + i,
+                     int(mis[i]) if i % 4 == 0 else 0) for i in range(count)]
+    # edge cases: empty, zero alpha, single row / column, ragged tails
+    probs += [Problem(0, 10), Problem(10, 0), Problem(7, 9, alpha=0.0), Problem(1, 1), Problem(1, 8193),
+              Problem(8193, 1), Problem(5, 3, pad=1), Problem(33, 4099, pad=2, misalign=1),
+              Problem(257, 4096), Problem(3, 8192, pad=4)]
+    return probs
+
+
+def check(probs, got):
+    for p, g in zip(probs, got):
+        want, scale = p.want()
+        if p.alpha == 0.0 or p.m == 0 or p.n == 0:
+            assert np.array_equal(g.view(np.uint32), p.c0.view(np.uint32)), (p.m, p.n)
+            continue
+        err = rel_err(g, want, scale)
+        assert err <= TOL, (p.m, p.n, p.ld, p.misalign, err)
+
+
+def test_mixed_batch_against_oracle():
+    probs = mixed()
+    got, b = run(probs)
+    assert b.tiles > 0
+    check(probs, got)
+
+
+def test_alone_equals_mix_bit_exact():
+    probs = mixed(seed=1)
+    got, _ = run(probs)
+    for i in (0, 5, 13, 41, len(probs) - 1, len(probs) - 3):
+        alone, _ = run([probs[i]])
+        assert np.array_equal(alone[0].view(np.uint32), got[i].view(np.uint32)), i
+
+
+def test_graph_replay_equals_launch_and_repeats_bit_identical():
+    probs = mixed(seed=2, count=30)
+    direct, _ = run(probs, launches=2)
+    graphed, _ = run(probs, graph=True, launches=2)
+    again, _ = run(probs, launches=2)
+    for a, b, c in zip(direct, graphed, again):
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+        assert np.array_equal(a.view(np.uint32), c.view(np.uint32))
+
+
+@pytest.mark.parametrize("lpr", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("u", [1, 2, 4])
+def test_every_kernel_variant(lpr, u):
+    table = gb.tuning_table({b: (lpr, u, 4096 if b % 2 else 65536) for b in range(gb.BATCH_BUCKETS)})
+    probs = [Problem(m, n, pad, 0.5, 100 + lpr * 10 + u, mis) for (m, n, pad, mis) in
+             ((1, 1, 0, 0), (3, 5, 1, 0), (300, 257, 0, 0), (97, 1027, 3, 0), (40, 4096, 0, 0),
+              (1000, 33, 0, 0), (17, 999, 0, 1), (2, 20000, 0, 0), (4097, 64, 0, 0))]
+    got, _ = run(probs, table=table)
+    check(probs, got)
+
+
+def test_empty_batch_is_a_no_op():
+    b = gb.Batch([])
+    assert b.tiles == 0
+    b.launch()
+    torch.cuda.synchronize()
+
+
+def test_full_size_workload_sampled():
+    """The 4096-problem workload of the batched benchmark, in its launch
+    configuration, checked against the oracle on sampled problems (the
+    largest, the smallest and seeded picks)."""
+    import bench
+    dev = torch.device("cuda", 0)
+    wl = bench.BatchWorkload(dev)
+    sizes = wl.m * wl.n
+    picks = sorted({int(np.argmax(sizes)), int(np.argmin(sizes))} |
+                   set(synth.integers(6, 0, 15, 0, len(wl.problems) - 1, np.int64).tolist()))
+    before = {}
+    for p in picks:
+        a, x, c = wl.operands(p)
+        before[p] = (a.cpu().numpy().ravel(), x.cpu().numpy(), c.cpu().numpy())
+    b = gb.Batch(wl.problems, table=gb.load_tuning(), device=dev)
+    b.launch()
+    torch.cuda.synchronize()
+    for p in picks:
+        A, x, c0 = before[p]
+        m, n, ld = int(wl.m[p]), int(wl.n[p]), int(wl.lda[p])
+        got = wl.operands(p)[2].cpu().numpy()
+        want = oracle.gemv(0, m, n, 1.0, A, ld, x, c0)
+        scale = oracle.gemv_scale(0, m, n, 1.0, A, ld, x, c0)
+        assert rel_err(got, want, scale) <= TOL, (p, m, n)
+    del wl, b
+    torch.cuda.empty_cache()
