@@ -46,14 +46,23 @@ struct BatchProblem {  // 48 bytes
   int32_t vec;  // A, x 16-byte aligned and lda a multiple of 4
 };
 
-struct BatchTile {  // 16 bytes
-  int32_t p, row0, rows;
-  uint8_t lpr_log2, u_log2, pad0, pad1;
+// A tile carries everything its rows need, so the kernel reads one
+// descriptor per tile and never the problem table.
+struct BatchTile {  // 48 bytes
+  const float* A;  // first row of the tile
+  const float* x;
+  float* c;        // output of the first row
+  int64_t lda;
+  int32_t rows, n;
+  float alpha;
+  uint8_t lpr_log2, u_log2, vec, pad;
 };
 
 static_assert(sizeof(BatchHeader) == 64, "plan header layout");
 static_assert(sizeof(BatchProblem) == 48, "plan problem layout");
-static_assert(sizeof(BatchTile) == 16, "plan tile layout");
+static_assert(sizeof(BatchTile) == 48, "plan tile layout");
+
+constexpr int kTileChunk = 32;  // tile descriptors staged in shared memory at a time
 
 // ----------------------------------------------------------------- kernel ---
 
@@ -74,8 +83,8 @@ __device__ __forceinline__ void fma4(float& acc, const float4& a, const float4& 
 // One lane's part of row `row`: packs lane, lane + lpr, ... (U in flight),
 // then the ragged columns past the last whole pack.
 template <int U>
-__device__ float row_vec(const BatchProblem& pb, int64_t row, int lane, int lpr) {
-  const float* Ar = pb.A + row * pb.lda;
+__device__ float row_vec(const BatchTile& pb, int r, int lane, int lpr) {
+  const float* Ar = pb.A + (int64_t)r * pb.lda;
   const float4* a = reinterpret_cast<const float4*>(Ar);
   const float4* xv = reinterpret_cast<const float4*>(pb.x);
   const int P = pb.n >> 2;
@@ -106,14 +115,14 @@ __device__ float row_vec(const BatchProblem& pb, int64_t row, int lane, int lpr)
       cnt = 0;
     }
   }
-  const int e = 4 * P + lane;
-  if (e < pb.n) acc = __fmaf_rn(__ldcs(Ar + e), __ldg(pb.x + e), acc);
+  for (int e = 4 * P + lane; e < pb.n; e += lpr)  // at most 3 columns, fewer lanes possible
+    acc = __fmaf_rn(__ldcs(Ar + e), __ldg(pb.x + e), acc);
   return __fadd_rn(hi, __fadd_rn(lo, acc));
 }
 
 // Misaligned problems: the lanes of the group stride over single elements.
-__device__ float row_scalar(const BatchProblem& pb, int64_t row, int lane, int lpr) {
-  const float* Ar = pb.A + row * pb.lda;
+__device__ float row_scalar(const BatchTile& pb, int r, int lane, int lpr) {
+  const float* Ar = pb.A + (int64_t)r * pb.lda;
   const int n = pb.n;
   float acc = 0.f, hi = 0.f, lo = 0.f;
   int cnt = 0;
@@ -149,40 +158,64 @@ __device__ __forceinline__ int64_t first_at_least(const int64_t* prefix, int64_t
   return lo;
 }
 
+// Copy tiles [t, t + k) of the plan into shared memory (16 bytes per lane).
+__device__ __forceinline__ void stage_tiles(BatchTile* dst, const BatchTile* src, int k) {
+  constexpr int kWords = (int)sizeof(BatchTile) / 16;
+  for (int i = threadIdx.x; i < k * kWords; i += kThreads)
+    cp_async_cg16(smem_u32(reinterpret_cast<const unsigned char*>(dst) + 16 * i),
+                  reinterpret_cast<const unsigned char*>(src) + 16 * i);
+  cp_async_commit();
+}
+
 __global__ void __launch_bounds__(kThreads, 3) gemv_batch_kernel(const unsigned char* __restrict__ plan) {
+  __shared__ __align__(16) BatchTile stage[2][kTileChunk];
   const BatchHeader* h = reinterpret_cast<const BatchHeader*>(plan);
   const int64_t T = h->tiles, B = h->total_cost;
-  const BatchProblem* probs = reinterpret_cast<const BatchProblem*>(plan + h->off_problems);
   const BatchTile* tiles = reinterpret_cast<const BatchTile*>(plan + h->off_tiles);
   const int64_t* prefix = reinterpret_cast<const int64_t*>(plan + h->off_prefix);
   const int64_t G = gridDim.x;
   const int64_t t0 = first_at_least(prefix, T, B * (int64_t)blockIdx.x / G);
   const int64_t t1 = first_at_least(prefix, T, B * ((int64_t)blockIdx.x + 1) / G);
+  if (t0 >= t1) return;  // uniform over the block
 
-  for (int64_t t = t0; t < t1; ++t) {
-    const BatchTile tl = tiles[t];
-    const BatchProblem pb = probs[tl.p];
-    const int lg = tl.lpr_log2;
-    const int lpr = 1 << lg;
-    const int lane = threadIdx.x & (lpr - 1);
-    const int wl = threadIdx.x & 31;
-    // the lanes of this thread's group (aligned run of lpr lanes of the warp)
-    const unsigned mask = lpr == 32 ? 0xffffffffu : ((1u << lpr) - 1u) << (wl & ~(lpr - 1));
-    for (int r = threadIdx.x >> lg; r < tl.rows; r += kThreads >> lg) {  // uniform over the group
-      const int64_t row = (int64_t)tl.row0 + r;
-      float v;
-      if (pb.vec) {
-        switch (tl.u_log2) {
-          case 0: v = row_vec<1>(pb, row, lane, lpr); break;
-          case 1: v = row_vec<2>(pb, row, lane, lpr); break;
-          default: v = row_vec<4>(pb, row, lane, lpr); break;
-        }
-      } else {
-        v = row_scalar(pb, row, lane, lpr);
-      }
-      for (int o = lpr >> 1; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(mask, v, o));
-      if (lane == 0) pb.c[row] = __fmaf_rn(pb.alpha, v, pb.c[row]);
+  // Tile descriptors arrive in chunks, the next chunk's copy in flight while
+  // the current one is processed.
+  auto chunk = [&](int64_t from) { return t1 - from < kTileChunk ? (int)(t1 - from) : kTileChunk; };
+  stage_tiles(stage[0], tiles + t0, chunk(t0));
+  int buf = 0;
+  for (int64_t c0 = t0; c0 < t1; c0 += kTileChunk, buf ^= 1) {
+    const int k = chunk(c0);
+    if (c0 + kTileChunk < t1) {
+      stage_tiles(stage[buf ^ 1], tiles + c0 + kTileChunk, chunk(c0 + kTileChunk));
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
+    __syncthreads();  // the current chunk is visible to every lane
+    for (int i = 0; i < k; ++i) {
+      const BatchTile pb = stage[buf][i];
+      const int lg = pb.lpr_log2;
+      const int lpr = 1 << lg;
+      const int lane = threadIdx.x & (lpr - 1);
+      const int wl = threadIdx.x & 31;
+      // the lanes of this thread's group (aligned run of lpr lanes of the warp)
+      const unsigned mask = lpr == 32 ? 0xffffffffu : ((1u << lpr) - 1u) << (wl & ~(lpr - 1));
+      for (int r = threadIdx.x >> lg; r < pb.rows; r += kThreads >> lg) {  // uniform over the group
+        float v;
+        if (pb.vec) {
+          switch (pb.u_log2) {
+            case 0: v = row_vec<1>(pb, r, lane, lpr); break;
+            case 1: v = row_vec<2>(pb, r, lane, lpr); break;
+            default: v = row_vec<4>(pb, r, lane, lpr); break;
+          }
+        } else {
+          v = row_scalar(pb, r, lane, lpr);
+        }
+        for (int o = lpr >> 1; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(mask, v, o));
+        if (lane == 0) pb.c[r] = __fmaf_rn(pb.alpha, v, pb.c[r]);
+      }
+    }
+    __syncthreads();  // every lane is done with this buffer before it is refilled
   }
 }
 
@@ -372,11 +405,16 @@ int gb_sgemv_batch_plan(int64_t count, const int64_t* m, const int64_t* n, const
     const int64_t R = tile_rows(n[p], tu);
     for (int64_t r0 = 0; r0 < m[p]; r0 += R) {
       BatchTile& tl = tiles[t];
-      tl.p = (int32_t)p;
-      tl.row0 = (int32_t)r0;
+      tl.A = A[p] + r0 * lda[p];
+      tl.x = x[p];
+      tl.c = c[p] + r0;
+      tl.lda = lda[p];
       tl.rows = (int32_t)std::min<int64_t>(R, m[p] - r0);
+      tl.n = (int32_t)n[p];
+      tl.alpha = alpha[p];
       tl.lpr_log2 = (uint8_t)log2_exact(tu.lanes_per_row);
       tl.u_log2 = (uint8_t)log2_exact(tu.packs_per_iter);
+      tl.vec = (uint8_t)pb.vec;
       prefix[t] = cost;
       cost += (int64_t)tl.rows * (4 * n[p] + 8) + 4 * n[p] + kTileOverhead;
       ++t;

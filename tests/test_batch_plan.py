@@ -20,8 +20,9 @@ HEADER = np.dtype([("magic", "<u4"), ("version", "<u4"), ("count", "<i8"), ("til
                    ("off_prefix", "<i8"), ("reserved", "<i8")])
 PROBLEM = np.dtype([("A", "<u8"), ("x", "<u8"), ("c", "<u8"), ("lda", "<i8"), ("m", "<i4"),
                     ("n", "<i4"), ("alpha", "<f4"), ("vec", "<i4")])
-TILE = np.dtype([("p", "<i4"), ("row0", "<i4"), ("rows", "<i4"), ("lpr_log2", "u1"),
-                 ("u_log2", "u1"), ("pad", "<u2")])
+TILE = np.dtype([("A", "<u8"), ("x", "<u8"), ("c", "<u8"), ("lda", "<i8"), ("rows", "<i4"),
+                 ("n", "<i4"), ("alpha", "<f4"), ("lpr_log2", "u1"), ("u_log2", "u1"), ("vec", "u1"),
+                 ("pad", "u1")])
 
 
 def log_uniform(count, seed, stream, lo, hi):
@@ -73,11 +74,22 @@ def aligned_buffer(nbytes):
 
 
 def decode(buf):
+    """Header, problems, tiles and cost prefix of a plan; each tile gets the
+    problem p it belongs to (the one whose c holds its output) and its first
+    row row0."""
     h = np.frombuffer(buf[:HEADER.itemsize].tobytes(), HEADER)[0]
     probs = np.frombuffer(buf[h["off_problems"]:h["off_problems"] + h["count"] * PROBLEM.itemsize].tobytes(),
                           PROBLEM)
-    tiles = np.frombuffer(buf[h["off_tiles"]:h["off_tiles"] + h["tiles"] * TILE.itemsize].tobytes(), TILE)
+    raw = np.frombuffer(buf[h["off_tiles"]:h["off_tiles"] + h["tiles"] * TILE.itemsize].tobytes(), TILE)
     prefix = np.frombuffer(buf[h["off_prefix"]:h["off_prefix"] + (h["tiles"] + 1) * 8].tobytes(), "<i8")
+    tiles = np.zeros(raw.size, dtype=TILE.descr + [("p", "<i8"), ("row0", "<i8")])
+    for f in TILE.names:
+        tiles[f] = raw[f]
+    if raw.size:
+        order = np.argsort(probs["c"])
+        k = np.searchsorted(probs["c"][order], raw["c"], side="right") - 1
+        tiles["p"] = order[k]
+        tiles["row0"] = (raw["c"] - probs["c"][tiles["p"]]) // 4
     return h, probs, tiles, prefix
 
 
@@ -107,6 +119,11 @@ def check_plan(fb, buf, table):
         assert np.all(np.diff(idx) == 1), "tiles of a problem are consecutive"
         starts = np.concatenate([[0], np.cumsum(mine["rows"])[:-1]])
         assert np.array_equal(mine["row0"], starts) and mine["rows"].sum() == fb.m[p]
+        a_row0 = fb.A[p] + np.uint64(4) * mine["row0"].astype(np.uint64) * np.uint64(fb.lda[p])
+        assert np.array_equal(mine["A"], a_row0)
+        assert np.all(mine["x"] == fb.x[p]) and np.all(mine["lda"] == fb.lda[p])
+        assert np.all(mine["n"] == fb.n[p]) and np.all(mine["alpha"] == fb.alpha[p])
+        assert np.all(mine["vec"] == pr["vec"])
         e = table[bucket(int(fb.n[p]))]
         assert np.all(mine["lpr_log2"] == int(np.log2(e.lanes_per_row)))
         assert np.all(mine["u_log2"] == int(np.log2(e.packs_per_iter)))
@@ -140,7 +157,7 @@ def test_random_batch_covers_every_row():
     assert st == gb.GB_OK
     h, probs, tiles, prefix = check_plan(fb, buf, table)
     # cost per tile: rows * (4n + 8) + 4n + 256
-    pn = probs["n"][tiles["p"]].astype(np.int64)
+    pn = tiles["n"].astype(np.int64)
     cost = tiles["rows"].astype(np.int64) * (4 * pn + 8) + 4 * pn + 256
     assert np.array_equal(np.diff(prefix), cost)
     # aligned fake addresses and lda = n + 3: only n = 1 (mod 4) rows are 16-byte multiples

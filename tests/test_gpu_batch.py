@@ -115,9 +115,13 @@ def test_graph_replay_equals_launch_and_repeats_bit_identical():
 @pytest.mark.parametrize("u", [1, 2, 4])
 def test_every_kernel_variant(lpr, u):
     table = gb.tuning_table({b: (lpr, u, 4096 if b % 2 else 65536) for b in range(gb.BATCH_BUCKETS)})
+    # (m, n, pad, misalign): lda = n + pad; the 16-byte path needs lda % 4 == 0,
+    # so the ragged columns of that path are covered by n % 4 = 1, 2, 3 with pad 3, 2, 1
     probs = [Problem(m, n, pad, 0.5, 100 + lpr * 10 + u, mis) for (m, n, pad, mis) in
              ((1, 1, 0, 0), (3, 5, 1, 0), (300, 257, 0, 0), (97, 1027, 3, 0), (40, 4096, 0, 0),
-              (1000, 33, 0, 0), (17, 999, 0, 1), (2, 20000, 0, 0), (4097, 64, 0, 0))]
+              (1000, 33, 0, 0), (17, 999, 0, 1), (2, 20000, 0, 0), (4097, 64, 0, 0),
+              (374, 59, 1, 0), (70, 61, 3, 0), (9, 4098, 2, 0), (300, 3, 1, 0), (5, 2, 2, 0),
+              (33, 1, 3, 0))]
     got, _ = run(probs, table=table)
     check(probs, got)
 
