@@ -595,6 +595,103 @@ def run_batched(device, stream, hbm, reps=5):
     return out
 
 
+# --------------------------------------------------------- serving leg --
+
+SERVE_WORKLOAD = ("Poisson request stream, 70% GEMV / 20% DOT / 10% GER, m and n log-uniform in "
+                  "[32, 16384], alpha 1, operands drawn on the device per request (counter-based "
+                  "generator) and resident until completion, 64 GB HBM admission budget, 4 streams")
+SERVE_BUDGET = 64 << 30
+
+
+def serve_stream(count, rate, seed, lo=32, hi=16384):
+    """Arrival offsets (ns), ops, m, n of a seeded Poisson stream."""
+    import numpy as np
+    import synth
+    u = (synth.uniform(count, seed, 501) + 1.0) / 2.0
+    t = np.cumsum(-np.log1p(-u) / rate * 1e9).astype(np.int64)
+    pick = (synth.uniform(count, seed, 502) + 1.0) / 2.0
+    ops = np.where(pick < 0.7, 0, np.where(pick < 0.9, 1, 2))
+    m = synth.log_uniform_integers(count, seed, 503, lo, hi)
+    n = synth.log_uniform_integers(count, seed, 504, lo, hi)
+    return t, ops, m, n
+
+
+def serve_once(count, rate, form, seed=0, sample=8):
+    """Serve one stream; returns throughput, latency percentiles and the
+    measured error of `sample` GEMV results (numpy FP64 on the generator's
+    FP32 values, relative to sum_j |A_ij x_j| + |c0_i|)."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2108_02025_gb300 as gb
+    t, ops, m, n = serve_stream(count, rate, seed)
+    gemv_idx = [i for i in range(count) if ops[i] == 0 and m[i] * n[i] <= 1 << 22]
+    picks = set(gemv_idx[::max(1, len(gemv_idx) // sample)][:sample])
+    outs = {}
+    with gb.Engine(SERVE_BUDGET, streams=4, max_inflight=16384, max_step_requests=512,
+                   table=gb.load_tuning()) as e:
+        t0 = e.now_ns() + int(0.2e9) + count * 20000   # every request is queued before the first arrives
+        for i in range(count):
+            out = None
+            if i in picks:
+                out = torch.empty(int(m[i]), dtype=torch.float32, pin_memory=True)
+                outs[i] = out
+            fi = form if ops[i] == 0 else gb.FORM_F32
+            st = e.submit(i, int(ops[i]), int(m[i]), int(n[i]), 1.0, seed * 1000003 + i, out,
+                          arrival_ns=int(t0 + t[i]), form=fi)
+            if st != gb.GB_OK:
+                raise RuntimeError(f"submit {i}: {st}")
+        if e.drain(600000) != gb.GB_OK:
+            raise RuntimeError("serving stream did not drain")
+        done = e.poll(count)
+        stats = e.stats()
+    bad = [c for c in done if c["status"] != gb.GB_OK]
+    if bad or len(done) != count:
+        raise RuntimeError(f"{len(bad)} failed requests, {len(done)} of {count} completed")
+    arr = np.array([c["arrival_ns"] for c in done], np.float64)
+    fin = np.array([c["done_ns"] for c in done], np.float64)
+    lat = (fin - arr) / 1e3
+    span = (fin.max() - arr.min()) / 1e9
+    steps = np.bincount([c["step"] for c in done])
+    err = 0.0
+    for i, out in outs.items():
+        mi, ni = int(m[i]), int(n[i])
+        ld = (ni + 7) // 8 * 8 if form == gb.FORM_BF16 else (ni + 3) // 4 * 4
+        s0 = seed * 1000003 + i
+        A = synth.uniform(mi * ld, s0, 1, np.float32).reshape(mi, ld)[:, :ni].astype(np.float64)
+        x = synth.uniform(ni, s0, 2, np.float32).astype(np.float64)
+        c0 = synth.uniform(mi, s0, 3, np.float32).astype(np.float64)
+        want = c0 + A @ x
+        scale = np.abs(c0) + np.abs(A) @ np.abs(x)
+        err = max(err, float(np.max(np.abs(out.numpy().astype(np.float64) - want) / scale)))
+    fp_bytes = np.where(ops == 0, (2 if form == gb.FORM_BF16 else 4) * m * n + 4 * n + 8 * m,
+                        np.where(ops == 1, 8 * n + 8, 8 * m * n + 4 * m + 4 * n)).sum()
+    return {"requests": count, "offered_per_s": rate, "solves_per_s": round(count / span, 1),
+            "p50_us": round(float(np.percentile(lat, 50)), 1),
+            "p99_us": round(float(np.percentile(lat, 99)), 1),
+            "compute_GB_s": round(float(fp_bytes) / span / 1e9, 1),
+            "steps": int(stats["steps"]), "mean_step_requests": round(float(steps.mean()), 1),
+            "steps_inflight_peak": int(stats["steps_inflight_peak"]),
+            "bytes_peak_GB": round(stats["bytes_peak"] / 1e9, 2),
+            "gemv_max_rel_err": float(f"{err:.3e}"), "gemv_err_sampled": len(outs)}
+
+
+def run_serving(count=20000):
+    """Saturating streams (throughput) for FP32 and BF16-stored A, then each
+    at half its measured throughput (latency under moderate load)."""
+    import paper_2108_02025_gb300 as gb
+    out = {"workload": SERVE_WORKLOAD, "budget_bytes": SERVE_BUDGET,
+           "error_bound": {"fp32": "1e-5 of sum|A x| + |c0| (FP32 accumulation)",
+                           "bf16": "2^-9 of sum|A x| + |c0| (BF16 rounding of A) + FP32 accumulation"}}
+    for name, form in (("fp32", gb.FORM_F32), ("bf16", gb.FORM_BF16)):
+        sat = serve_once(count, 1e7, form, seed=1)
+        mod = serve_once(count // 2, sat["solves_per_s"] * 0.5, form, seed=2)
+        out[name] = {"saturated": sat, "half_load": mod}
+    out["bf16_speedup_solves"] = round(out["bf16"]["saturated"]["solves_per_s"] /
+                                       out["fp32"]["saturated"]["solves_per_s"], 3)
+    return out
+
+
 # ------------------------------------------------------------------- arms --
 
 def run_ours(args):
@@ -658,10 +755,11 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(wl, stream, device, bytes_step, args, world)
 
-    precision = batched = None
+    precision = batched = serving = None
     if not args.no_growth:
         precision = run_precision(device, stream)
         batched = run_batched(device, stream, hbm)
+        serving = run_serving()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -696,6 +794,7 @@ def run_ours(args):
             "ops": ops_report,
             "precision": precision,
             "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -266,12 +266,49 @@ int gb_sgemv_batch_plan(int64_t count, const int64_t *m, const int64_t *n, const
                         size_t plan_bytes);
 
 /* Enqueue the batch on `stream`: one launch.  plan_host (1) is the host
-   plan (read for the launch size), plan_dev (2) its device copy.  Returns
+   plan (from gb_sgemv_batch_plan or gb_batch_plan; read for the launch
+   size), plan_dev (2) its device copy.  Returns
    GB_OK, -1 (not a plan), -2 (plan_dev NULL or misaligned) or GB_ERR_CUDA. */
 int gb_sgemv_batch(const void *plan_host, const void *plan_dev, gb_stream stream);
 
 /* Number of tiles in a host plan (-1 if it is not a plan). */
 int64_t gb_sgemv_batch_tiles(const void *plan_host);
+
+/* Mixed batches: GEMVs with FP32 or BF16-stored A and GERs in one plan, run
+   by the same launch (gb_sgemv_batch).  Problem p is described by an item:
+     GB_BATCH_GEMV_F32   c <- c + alpha A x, A FP32 m x n (lda elements)
+     GB_BATCH_GEMV_BF16  the same with A stored as BF16 codes (uint16, the
+                         top half of the binary32, decoded exactly)
+     GB_BATCH_GER_F32    C <- C + alpha x y^T as fma(x_i, fl(alpha y_j), C_ij)
+                         (bit-exact, as gb_sger), C FP32 m x n (lda)
+   Item fields: A = the matrix (GEMV: read; GER: C, read and written);
+   x = the n-vector (GEMV: x; GER: y); c = the m-vector (GEMV: c, read and
+   written; GER: x, read).  Items with m, n or alpha zero are skipped.  The
+   16-byte path needs A and x 16-byte aligned and lda * element bytes a
+   multiple of 16; otherwise a scalar path runs in the same launch.  No
+   output (GEMV c, GER C) may overlap another output or any input.
+   gb_batch_plan returns GB_OK, -1 (count < 0), -2 (an invalid item: kind,
+   shape, lda, a NULL pointer of an active item, an overlap), -3 (table),
+   -4 (plan NULL or misaligned), -5 (plan_bytes too small).
+   gb_batch_plan_bytes returns 0 for an invalid count, kind, shape or table. */
+typedef enum {
+  GB_BATCH_GEMV_F32 = 0,
+  GB_BATCH_GEMV_BF16 = 1,
+  GB_BATCH_GER_F32 = 2
+} gb_batch_kind;
+typedef struct {
+  int32_t kind;     /* gb_batch_kind */
+  int32_t reserved; /* 0 */
+  int64_t m, n, lda;
+  float alpha;
+  int32_t reserved2; /* 0 */
+  void *A;
+  const float *x;
+  float *c;
+} gb_batch_item;
+size_t gb_batch_plan_bytes(int64_t count, const gb_batch_item *items, const gb_batch_tuning *table);
+int gb_batch_plan(int64_t count, const gb_batch_item *items, const gb_batch_tuning *table, void *plan,
+                  size_t plan_bytes);
 
 /* GEMV without allocation.  The paper has no counterpart: this entry point
    exists for callers that cannot allocate device memory (code running where

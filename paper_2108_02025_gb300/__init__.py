@@ -68,10 +68,21 @@ def _load() -> ctypes.CDLL:
     lib.gb_sgemv_batch_plan.argtypes = [I64, P, P, P, P, P, P, P, P, P, SZ]
     lib.gb_sgemv_batch.argtypes = [P, P, P]
     lib.gb_sgemv_batch_tiles.argtypes, lib.gb_sgemv_batch_tiles.restype = [P], I64
+    lib.gb_batch_plan_bytes.argtypes, lib.gb_batch_plan_bytes.restype = [I64, P, P], SZ
+    lib.gb_batch_plan.argtypes, lib.gb_batch_plan.restype = [I64, P, P, P, SZ], I
     for name in ("gb_dgemv", "gb_sgemv", "gb_ddot", "gb_sdot", "gb_dger", "gb_sger",
                  "gb_dgemv_noalloc", "gb_quantize_bf16", "gb_quantize_e4m3", "gb_gemv_bf16",
                  "gb_gemv_e4m3", "gb_sgemv_batch_plan", "gb_sgemv_batch"):
         getattr(lib, name).restype = I
+    # serving engine (include/gbserve.h)
+    lib.gb_engine_now_ns.argtypes, lib.gb_engine_now_ns.restype = [], I64
+    lib.gb_engine_create.argtypes, lib.gb_engine_create.restype = [P, P], I
+    lib.gb_engine_submit.argtypes, lib.gb_engine_submit.restype = [P, P], I
+    lib.gb_engine_poll.argtypes, lib.gb_engine_poll.restype = [P, P, I], I
+    lib.gb_engine_drain.argtypes, lib.gb_engine_drain.restype = [P, I64], I
+    lib.gb_engine_stats_get.argtypes, lib.gb_engine_stats_get.restype = [P, P], I
+    lib.gb_engine_request_bytes.argtypes, lib.gb_engine_request_bytes.restype = [P], SZ
+    lib.gb_engine_destroy.argtypes, lib.gb_engine_destroy.restype = [P], None
     return lib
 
 
@@ -82,7 +93,14 @@ EXPORTS = ("gb_version", "gb_status_string", "gb_workspace_bytes", "gb_workspace
            "gb_dgemv", "gb_sgemv", "gb_ddot", "gb_sdot", "gb_dger", "gb_sger",
            "gb_dgemv_noalloc", "gb_quantize_bf16", "gb_quantize_e4m3", "gb_gemv_bf16",
            "gb_gemv_e4m3", "gb_sgemv_batch_default_tuning", "gb_sgemv_batch_plan_bytes",
-           "gb_sgemv_batch_plan", "gb_sgemv_batch", "gb_sgemv_batch_tiles")
+           "gb_sgemv_batch_plan", "gb_sgemv_batch", "gb_sgemv_batch_tiles", "gb_batch_plan_bytes",
+           "gb_batch_plan")
+
+
+# Every symbol include/gbserve.h declares.
+ENGINE_EXPORTS = ("gb_engine_now_ns", "gb_engine_create", "gb_engine_submit", "gb_engine_poll",
+                  "gb_engine_drain", "gb_engine_stats_get", "gb_engine_request_bytes",
+                  "gb_engine_destroy")
 
 
 def lib() -> ctypes.CDLL:
@@ -190,6 +208,24 @@ class BatchTuning(ctypes.Structure):
 
 
 TuningTable = BatchTuning * BATCH_BUCKETS
+BATCH_GEMV_F32, BATCH_GEMV_BF16, BATCH_GER_F32 = 0, 1, 2
+
+
+class BatchItem(ctypes.Structure):
+    """gb_batch_item: A = the matrix (GEMV A or BF16 codes; GER C), x = the
+    n-vector (GEMV x; GER y), c = the m-vector (GEMV c; GER x)."""
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("m", ctypes.c_int64),
+                ("n", ctypes.c_int64), ("lda", ctypes.c_int64), ("alpha", ctypes.c_float),
+                ("reserved2", ctypes.c_int32), ("A", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("c", ctypes.c_void_p)]
+
+
+def gb_batch_plan_bytes(count, items, table=None) -> int:
+    return _lib.gb_batch_plan_bytes(count, _addr(items), _addr(table))
+
+
+def gb_batch_plan(count, items, table, plan, plan_bytes) -> int:
+    return _lib.gb_batch_plan(count, _addr(items), _addr(table), _addr(plan), plan_bytes)
 
 
 def _addr(buf) -> int | None:
@@ -250,6 +286,13 @@ def load_tuning(path: str | None = None):
     return tuning_table({int(b): tuple(v) for b, v in d["buckets"].items()})
 
 
+def _aligned_host(nbytes):
+    import numpy as np
+    raw = np.zeros(nbytes + 16, np.uint8)
+    off = (-raw.ctypes.data) % 16
+    return raw[off:off + nbytes]
+
+
 class Batch:
     """A planned batch of FP32 row-major GEMVs c_p += alpha_p A_p x_p, run by
     one persistent launch (``launch``) or by replaying a captured CUDA graph
@@ -281,11 +324,30 @@ class Batch:
         nb = gb_sgemv_batch_plan_bytes(count, m, n, alpha, self.table)
         if nb == 0:
             raise GbError(-1, "sgemv_batch_plan_bytes")
-        self.host = np.zeros(nb + 16, np.uint8)
-        off = (-self.host.ctypes.data) % 16
-        self.host = self.host[off:off + nb]
+        self.host = _aligned_host(nb)
         _check(gb_sgemv_batch_plan(count, m, n, lda, alpha, A, x, c, self.table, self.host, nb),
                "sgemv_batch_plan")
+        self._upload(count, device)
+
+    @classmethod
+    def from_items(cls, items, table=None, device=None):
+        """A mixed batch: ``items`` is a list of (kind, A, x, c, alpha, m, n, lda)
+        with the gb_batch_item meaning of A, x and c (tensors or addresses)."""
+        self = cls.__new__(cls)
+        arr = (BatchItem * max(1, len(items)))()
+        for i, (kind, a, xv, cv, al, mi, ni, ld) in enumerate(items):
+            arr[i] = BatchItem(kind, 0, mi, ni, ld, al, 0, _ptr(a) or 0, _ptr(xv) or 0, _ptr(cv) or 0)
+        self.table = tuning_table() if table is None else table
+        nb = gb_batch_plan_bytes(len(items), arr, self.table)
+        if nb == 0:
+            raise GbError(-2, "batch_plan_bytes")
+        self.host = _aligned_host(nb)
+        _check(gb_batch_plan(len(items), arr, self.table, self.host, nb), "batch_plan")
+        self._upload(len(items), device)
+        return self
+
+    def _upload(self, count, device):
+        import torch
         dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.dev = torch.from_numpy(self.host.copy()).to(dev)
         torch.cuda.synchronize(dev)
@@ -308,6 +370,148 @@ class Batch:
 
     def replay(self) -> None:
         self.graph.replay()
+
+
+# -------------------------------------------------------- serving engine --
+
+GB_ERR_BUDGET = -104
+GB_ERR_TIMEOUT = -105
+REQ_GEMV, REQ_DOT, REQ_GER = 0, 1, 2
+FORM_F32, FORM_BF16 = 0, 1
+ENGINE_HOST_ONLY = 1
+
+
+class EngineConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("streams", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("max_step_requests", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("sim_bytes_per_ns", ctypes.c_double),
+                ("table", ctypes.c_void_p)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("op", ctypes.c_int32), ("form", ctypes.c_int32),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("alpha", ctypes.c_float),
+                ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64), ("out", ctypes.c_void_p),
+                ("arrival_ns", ctypes.c_int64)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("op", ctypes.c_int32),
+                ("arrival_ns", ctypes.c_int64), ("admitted_ns", ctypes.c_int64),
+                ("launched_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64),
+                ("step", ctypes.c_int64), ("bytes", ctypes.c_int64)]
+
+
+class EngineStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("inflight_peak", ctypes.c_int64), ("steps_inflight_peak", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t),
+                ("budget_bytes", ctypes.c_size_t)]
+
+
+def gb_engine_now_ns() -> int:
+    return _lib.gb_engine_now_ns()
+
+
+def gb_engine_create(cfg, out) -> int:
+    return _lib.gb_engine_create(_addr(cfg), _addr(out))
+
+
+def gb_engine_submit(engine, request) -> int:
+    return _lib.gb_engine_submit(engine, _addr(request))
+
+
+def gb_engine_poll(engine, out, max_count) -> int:
+    return _lib.gb_engine_poll(engine, _addr(out), max_count)
+
+
+def gb_engine_drain(engine, timeout_ms) -> int:
+    return _lib.gb_engine_drain(engine, timeout_ms)
+
+
+def gb_engine_stats_get(engine, out) -> int:
+    return _lib.gb_engine_stats_get(engine, _addr(out))
+
+
+def gb_engine_request_bytes(request) -> int:
+    return _lib.gb_engine_request_bytes(_addr(request))
+
+
+def gb_engine_destroy(engine) -> None:
+    _lib.gb_engine_destroy(engine)
+
+
+class Engine:
+    """The serving engine (continuous batching under an HBM budget).
+
+    ``submit`` queues a request (op, m, n, alpha, seed, optional pinned host
+    tensor for the result, arrival time on ``now_ns``'s clock); ``drain``
+    waits for all of them; ``poll`` returns the completions as dicts."""
+
+    def __init__(self, budget_bytes, streams=4, max_inflight=4096, max_step_requests=256,
+                 host_only=False, sim_bytes_per_ns=1000.0, table=None):
+        self.table = table
+        cfg = EngineConfig(budget_bytes, streams, max_inflight, max_step_requests,
+                           ENGINE_HOST_ONLY if host_only else 0, sim_bytes_per_ns,
+                           _addr(table) if table is not None else None)
+        h = ctypes.c_void_p()
+        _check(gb_engine_create(cfg, ctypes.addressof(h)), "engine_create")
+        self.h = h.value
+        self._keep = {}
+
+    @staticmethod
+    def now_ns() -> int:
+        return gb_engine_now_ns()
+
+    def submit(self, rid, op, m, n, alpha=1.0, seed=0, out=None, arrival_ns=0, form=FORM_F32) -> int:
+        """Returns the status (GB_OK, -2 invalid, GB_ERR_BUDGET)."""
+        r = Request(rid, op, form, m, n, alpha, 0, seed, _ptr(out), arrival_ns)
+        st = gb_engine_submit(self.h, ctypes.addressof(r))
+        if st == GB_OK and out is not None:
+            self._keep[rid] = out  # the engine writes into it later
+        return st
+
+    def drain(self, timeout_ms=60000) -> int:
+        return gb_engine_drain(self.h, timeout_ms)
+
+    def poll(self, max_count=1 << 16):
+        buf = (Completion * max_count)()
+        k = gb_engine_poll(self.h, buf, max_count)
+        if k < 0:
+            raise GbError(k, "engine_poll")
+        out = []
+        for c in buf[:k]:
+            out.append({f: getattr(c, f) for f, _ in Completion._fields_})
+            self._keep.pop(c.id, None)
+        return out
+
+    def stats(self) -> dict:
+        s = EngineStats()
+        _check(gb_engine_stats_get(self.h, ctypes.addressof(s)), "engine_stats")
+        return {f: getattr(s, f) for f, _ in EngineStats._fields_}
+
+    def close(self) -> None:
+        if self.h:
+            gb_engine_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def request_bytes(op, m, n, form=FORM_F32) -> int:
+    r = Request(0, op, form, m, n, 1.0, 0, 0, None, 0)
+    return gb_engine_request_bytes(ctypes.addressof(r))
 
 
 # ---------------------------------------------------------- convenience ----

@@ -281,7 +281,7 @@ inline SplitShape qgemv_shape(int fmt, int64_t m, int64_t n) {
 struct Inject {
   int op = -1;
   long long nth = 0;
-  std::atomic<long long> count[3] = {0, 0, 0};
+  std::atomic<long long> count[kInjectSites] = {0, 0, 0, 0};
 };
 
 Inject& inject() {
@@ -296,6 +296,7 @@ Inject& inject() {
     if (len == 4 && std::strncmp(v, "gemv", 4) == 0) inj.op = GB_OP_GEMV;
     else if (len == 3 && std::strncmp(v, "dot", 3) == 0) inj.op = GB_OP_DOT;
     else if (len == 3 && std::strncmp(v, "ger", 3) == 0) inj.op = GB_OP_GER;
+    else if (len == 4 && std::strncmp(v, "step", 4) == 0) inj.op = kInjectStep;
     inj.nth = std::atoll(colon + 1);
   });
   return inj;
@@ -446,6 +447,8 @@ int qgemv(int fmt, int64_t m, int64_t n, float alpha, const void* Q, int64_t ldq
 }
 
 }  // namespace
+
+bool fault_injected(int site) { return injected(site); }
 
 // Occupancy of each kernel is queried once per (kernel, device).
 int grid_size(const void* kernel, int64_t units, size_t smem) {

@@ -1,18 +1,22 @@
-// Batched FP32 GEMV: many independent row-major problems
-//     c_p <- c_p + alpha_p * A_p x_p          (Def. GEMV, Sec. 3.1, per problem)
-// in ONE persistent launch.  The paper runs one GEMV at a time and notes that
-// small problems do not amortise the cost of starting threads (Sec. 4.1, the
-// speedup bound with its thread overhead O(t); Sec. 4.2, Analysis); on the
-// GPU the analogue is a launch, and its drain, per small GEMV.  Here a host
-// planner cuts every problem into tiles of whole rows of about equal bytes,
-// and each block of one launch streams the tiles whose cost prefix falls in
-// its equal share [b*B/G, (b+1)*B/G).
+// Batched level-2 work: many independent row-major problems in ONE
+// persistent launch,
+//     GEMV  c_p <- c_p + alpha_p * A_p x_p   (Def. GEMV, Sec. 3.1; A FP32 or BF16)
+//     GER   C_p <- C_p + alpha_p * x_p y_p^T (Def. GEM; one fma per element)
+// The paper runs one GEMV at a time and notes that small problems do not
+// amortise the cost of starting threads (Sec. 4.1, the speedup bound with
+// its thread overhead O(t); Sec. 4.2, Analysis); on the GPU the analogue is
+// a launch, and its drain, per small problem.  A host planner cuts every
+// problem into tiles of whole rows of about equal cost, and each block of
+// one launch streams the tiles whose cost prefix falls in its equal share
+// [b*B/G, (b+1)*B/G).  The public entry points plan FP32 GEMVs; the serving
+// engine plans all three kinds through the same planner.
 //
-// Within a tile, groups of `lpr` lanes each sum one row: every lane keeps
-// FP32 fma chains of at most 64 products folded into a compensated FP32 sum
-// (TwoSum), and the group combines its lanes by a fixed butterfly.  A row's
-// result therefore depends only on n and the tuning entry of n's bucket,
-// never on the other problems, the tile boundaries or the grid.
+// Within a tile, groups of `lpr` lanes each take one row.  GEMV: every lane
+// keeps FP32 fma chains of at most 64 products folded into a compensated
+// FP32 sum (TwoSum), and the group combines its lanes by a fixed butterfly;
+// a row's result therefore depends only on n and the tuning entry of n's
+// bucket, never on the other problems, the tile boundaries or the grid.
+// GER: every element is one fma, independent of any tiling.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -37,25 +41,28 @@ struct BatchHeader {  // 64 bytes
 };
 
 struct BatchProblem {  // 48 bytes
-  const float* A;
-  const float* x;
-  float* c;
-  int64_t lda;
+  const void* A;  // GEMV: A (FP32) or its BF16 codes; GER: C (read and written)
+  const float* x; // GEMV: x; GER: y (the n-vector)
+  float* c;       // GEMV: c (read and written); GER: x (the m-vector, read)
+  int64_t lda;    // elements
   int32_t m, n;
   float alpha;
-  int32_t vec;  // A, x 16-byte aligned and lda a multiple of 4
+  uint8_t vec;    // 16-byte path: matrix and n-vector 16-byte aligned, lda a multiple of a pack
+  uint8_t kind;   // BatchKind
+  uint16_t pad;
 };
 
 // A tile carries everything its rows need, so the kernel reads one
-// descriptor per tile and never the problem table.
+// descriptor per tile and never the problem table.  Fields as in
+// BatchProblem, A and c moved to the tile's first row.
 struct BatchTile {  // 48 bytes
-  const float* A;  // first row of the tile
+  const void* A;
   const float* x;
-  float* c;        // output of the first row
+  float* c;
   int64_t lda;
   int32_t rows, n;
   float alpha;
-  uint8_t lpr_log2, u_log2, vec, pad;
+  uint8_t lpr_log2, u_log2, vec, kind;
 };
 
 static_assert(sizeof(BatchHeader) == 64, "plan header layout");
@@ -73,57 +80,101 @@ __device__ __forceinline__ void fold(float& acc, float& hi, float& lo) {
   acc = 0.f;
 }
 
-__device__ __forceinline__ void fma4(float& acc, const float4& a, const float4& x) {
-  acc = __fmaf_rn(a.x, x.x, acc);
-  acc = __fmaf_rn(a.y, x.y, acc);
-  acc = __fmaf_rn(a.z, x.z, acc);
-  acc = __fmaf_rn(a.w, x.w, acc);
-}
+// A 16-byte pack of the matrix: 4 FP32 values, or 8 BF16 codes decoded
+// exactly (a BF16 value is the top half of its binary32).
+template <int KIND>
+struct Row;
 
-// One lane's part of row `row`: packs lane, lane + lpr, ... (U in flight),
-// then the ragged columns past the last whole pack.
-template <int U>
-__device__ float row_vec(const BatchTile& pb, int r, int lane, int lpr) {
-  const float* Ar = pb.A + (int64_t)r * pb.lda;
-  const float4* a = reinterpret_cast<const float4*>(Ar);
-  const float4* xv = reinterpret_cast<const float4*>(pb.x);
-  const int P = pb.n >> 2;
+template <>
+struct Row<kBatchGemvF32> {
+  static constexpr int PER = 4;
+  __device__ static float elem(const void* row, int e) { return __ldcs(static_cast<const float*>(row) + e); }
+  __device__ static void pack(const void* row, int j, float (&v)[PER]) {
+    const float4 a = __ldcs(static_cast<const float4*>(row) + j);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
+};
+
+template <>
+struct Row<kBatchGemvBF16> {
+  static constexpr int PER = 8;
+  __device__ static float elem(const void* row, int e) {
+    return __uint_as_float((unsigned)__ldcs(static_cast<const unsigned short*>(row) + e) << 16);
+  }
+  __device__ static void pack(const void* row, int j, float (&v)[PER]) {
+    const uint4 a = __ldcs(static_cast<const uint4*>(row) + j);
+    const unsigned w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[2 * k] = __uint_as_float(w[k] << 16);
+      v[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+    }
+  }
+};
+
+// One lane's part of the dot product of row r with x: packs lane, lane +
+// lpr, ... (U in flight), then the ragged columns past the last whole pack.
+template <int KIND, int U>
+__device__ float row_dot_vec(const BatchTile& tl, int r, int lane, int lpr) {
+  using R = Row<KIND>;
+  constexpr int PER = R::PER;
+  const void* row = static_cast<const unsigned char*>(tl.A) + (int64_t)r * tl.lda * (KIND == kBatchGemvBF16 ? 2 : 4);
+  const float4* xv = reinterpret_cast<const float4*>(tl.x);
+  const int P = tl.n / PER;
   float acc = 0.f, hi = 0.f, lo = 0.f;
   int cnt = 0;
   int j = lane;
 #pragma unroll 1
   for (; j + (U - 1) * lpr < P; j += U * lpr) {
-    float4 av[U], xx[U];
+    float av[U][PER];
 #pragma unroll
-    for (int q = 0; q < U; ++q) av[q] = __ldcs(a + j + q * lpr);
+    for (int q = 0; q < U; ++q) R::pack(row, j + q * lpr, av[q]);
 #pragma unroll
-    for (int q = 0; q < U; ++q) xx[q] = __ldg(xv + j + q * lpr);
+    for (int q = 0; q < U; ++q) {
 #pragma unroll
-    for (int q = 0; q < U; ++q) fma4(acc, av[q], xx[q]);
-    cnt += 4 * U;
-    if (cnt == 64) {  // 4U divides 64
+      for (int k = 0; k < PER / 4; ++k) {
+        const float4 x4 = __ldg(xv + (j + q * lpr) * (PER / 4) + k);
+        acc = __fmaf_rn(av[q][4 * k + 0], x4.x, acc);
+        acc = __fmaf_rn(av[q][4 * k + 1], x4.y, acc);
+        acc = __fmaf_rn(av[q][4 * k + 2], x4.z, acc);
+        acc = __fmaf_rn(av[q][4 * k + 3], x4.w, acc);
+      }
+    }
+    cnt += PER * U;
+    if (cnt == 64) {  // PER * U divides 64
       fold(acc, hi, lo);
       cnt = 0;
     }
   }
 #pragma unroll 1
   for (; j < P; j += lpr) {
-    fma4(acc, __ldcs(a + j), __ldg(xv + j));
-    cnt += 4;
+    float av[PER];
+    R::pack(row, j, av);
+#pragma unroll
+    for (int k = 0; k < PER / 4; ++k) {
+      const float4 x4 = __ldg(xv + j * (PER / 4) + k);
+      acc = __fmaf_rn(av[4 * k + 0], x4.x, acc);
+      acc = __fmaf_rn(av[4 * k + 1], x4.y, acc);
+      acc = __fmaf_rn(av[4 * k + 2], x4.z, acc);
+      acc = __fmaf_rn(av[4 * k + 3], x4.w, acc);
+    }
+    cnt += PER;
     if (cnt == 64) {
       fold(acc, hi, lo);
       cnt = 0;
     }
   }
-  for (int e = 4 * P + lane; e < pb.n; e += lpr)  // at most 3 columns, fewer lanes possible
-    acc = __fmaf_rn(__ldcs(Ar + e), __ldg(pb.x + e), acc);
+  for (int e = PER * P + lane; e < tl.n; e += lpr)  // fewer than PER columns, possibly fewer lanes
+    acc = __fmaf_rn(R::elem(row, e), __ldg(tl.x + e), acc);
   return __fadd_rn(hi, __fadd_rn(lo, acc));
 }
 
 // Misaligned problems: the lanes of the group stride over single elements.
-__device__ float row_scalar(const BatchTile& pb, int r, int lane, int lpr) {
-  const float* Ar = pb.A + (int64_t)r * pb.lda;
-  const int n = pb.n;
+template <int KIND>
+__device__ float row_dot_scalar(const BatchTile& tl, int r, int lane, int lpr) {
+  using R = Row<KIND>;
+  const void* row = static_cast<const unsigned char*>(tl.A) + (int64_t)r * tl.lda * (KIND == kBatchGemvBF16 ? 2 : 4);
+  const int n = tl.n;
   float acc = 0.f, hi = 0.f, lo = 0.f;
   int cnt = 0;
   int j = lane;
@@ -131,9 +182,9 @@ __device__ float row_scalar(const BatchTile& pb, int r, int lane, int lpr) {
   for (; j + 3 * lpr < n; j += 4 * lpr) {
     float a[4], x[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) a[q] = __ldcs(Ar + j + q * lpr);
+    for (int q = 0; q < 4; ++q) a[q] = R::elem(row, j + q * lpr);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) x[q] = __ldg(pb.x + j + q * lpr);
+    for (int q = 0; q < 4; ++q) x[q] = __ldg(tl.x + j + q * lpr);
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc = __fmaf_rn(a[q], x[q], acc);
     cnt += 4;
@@ -143,8 +194,74 @@ __device__ float row_scalar(const BatchTile& pb, int r, int lane, int lpr) {
     }
   }
 #pragma unroll 1
-  for (; j < n; j += lpr) acc = __fmaf_rn(__ldcs(Ar + j), __ldg(pb.x + j), acc);
+  for (; j < n; j += lpr) acc = __fmaf_rn(R::elem(row, j), __ldg(tl.x + j), acc);
   return __fadd_rn(hi, __fadd_rn(lo, acc));
+}
+
+// GER row r: C_rj <- fma(x_r, fl(alpha * y_j), C_rj), U packs per lane in flight.
+template <int U>
+__device__ void row_ger_vec(const BatchTile& tl, int r, int lane, int lpr) {
+  float* row = static_cast<float*>(const_cast<void*>(tl.A)) + (int64_t)r * tl.lda;
+  float4* cv = reinterpret_cast<float4*>(row);
+  const float4* yv = reinterpret_cast<const float4*>(tl.x);
+  const float xr = tl.c[r];
+  const float al = tl.alpha;
+  const int P = tl.n >> 2;
+  int j = lane;
+#pragma unroll 1
+  for (; j + (U - 1) * lpr < P; j += U * lpr) {
+    float4 cc[U], yy[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) cc[q] = __ldcs(cv + j + q * lpr);
+#pragma unroll
+    for (int q = 0; q < U; ++q) yy[q] = __ldg(yv + j + q * lpr);
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      cc[q].x = __fmaf_rn(xr, __fmul_rn(al, yy[q].x), cc[q].x);
+      cc[q].y = __fmaf_rn(xr, __fmul_rn(al, yy[q].y), cc[q].y);
+      cc[q].z = __fmaf_rn(xr, __fmul_rn(al, yy[q].z), cc[q].z);
+      cc[q].w = __fmaf_rn(xr, __fmul_rn(al, yy[q].w), cc[q].w);
+      __stcs(cv + j + q * lpr, cc[q]);
+    }
+  }
+#pragma unroll 1
+  for (; j < P; j += lpr) {
+    float4 c4 = __ldcs(cv + j);
+    const float4 y4 = __ldg(yv + j);
+    c4.x = __fmaf_rn(xr, __fmul_rn(al, y4.x), c4.x);
+    c4.y = __fmaf_rn(xr, __fmul_rn(al, y4.y), c4.y);
+    c4.z = __fmaf_rn(xr, __fmul_rn(al, y4.z), c4.z);
+    c4.w = __fmaf_rn(xr, __fmul_rn(al, y4.w), c4.w);
+    __stcs(cv + j, c4);
+  }
+  for (int e = 4 * P + lane; e < tl.n; e += lpr) row[e] = __fmaf_rn(xr, __fmul_rn(al, __ldg(tl.x + e)), row[e]);
+}
+
+__device__ void row_ger_scalar(const BatchTile& tl, int r, int lane, int lpr) {
+  float* row = static_cast<float*>(const_cast<void*>(tl.A)) + (int64_t)r * tl.lda;
+  const float xr = tl.c[r];
+  const float al = tl.alpha;
+#pragma unroll 1
+  for (int j = lane; j < tl.n; j += lpr) row[j] = __fmaf_rn(xr, __fmul_rn(al, __ldg(tl.x + j)), row[j]);
+}
+
+template <int KIND>
+__device__ __forceinline__ float row_dot(const BatchTile& tl, int r, int lane, int lpr) {
+  if (!tl.vec) return row_dot_scalar<KIND>(tl, r, lane, lpr);
+  switch (tl.u_log2) {
+    case 0: return row_dot_vec<KIND, 1>(tl, r, lane, lpr);
+    case 1: return row_dot_vec<KIND, 2>(tl, r, lane, lpr);
+    default: return row_dot_vec<KIND, 4>(tl, r, lane, lpr);
+  }
+}
+
+__device__ __forceinline__ void row_ger(const BatchTile& tl, int r, int lane, int lpr) {
+  if (!tl.vec) return row_ger_scalar(tl, r, lane, lpr);
+  switch (tl.u_log2) {
+    case 0: return row_ger_vec<1>(tl, r, lane, lpr);
+    case 1: return row_ger_vec<2>(tl, r, lane, lpr);
+    default: return row_ger_vec<4>(tl, r, lane, lpr);
+  }
 }
 
 // First t in [0, T] with prefix[t] >= v (prefix[0] = 0, prefix[T] = B).
@@ -201,16 +318,12 @@ __global__ void __launch_bounds__(kThreads, 3) gemv_batch_kernel(const unsigned 
       // the lanes of this thread's group (aligned run of lpr lanes of the warp)
       const unsigned mask = lpr == 32 ? 0xffffffffu : ((1u << lpr) - 1u) << (wl & ~(lpr - 1));
       for (int r = threadIdx.x >> lg; r < pb.rows; r += kThreads >> lg) {  // uniform over the group
-        float v;
-        if (pb.vec) {
-          switch (pb.u_log2) {
-            case 0: v = row_vec<1>(pb, r, lane, lpr); break;
-            case 1: v = row_vec<2>(pb, r, lane, lpr); break;
-            default: v = row_vec<4>(pb, r, lane, lpr); break;
-          }
-        } else {
-          v = row_scalar(pb, r, lane, lpr);
+        if (pb.kind == kBatchGerF32) {
+          row_ger(pb, r, lane, lpr);
+          continue;
         }
+        float v = pb.kind == kBatchGemvBF16 ? row_dot<kBatchGemvBF16>(pb, r, lane, lpr)
+                                            : row_dot<kBatchGemvF32>(pb, r, lane, lpr);
         for (int o = lpr >> 1; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(mask, v, o));
         if (lane == 0) pb.c[r] = __fmaf_rn(pb.alpha, v, pb.c[r]);
       }
@@ -242,25 +355,37 @@ inline bool tuning_ok(const gb_batch_tuning& t) {
   return l >= 0 && l <= 5 && u >= 0 && u <= 2 && t.tile_bytes >= 4096 && t.reserved == 0;
 }
 
-// Rows per tile for a problem of n columns: about tile_bytes of A, a
-// multiple of the block's row groups (256 / lpr), at least one group each.
-inline int64_t tile_rows(int64_t n, const gb_batch_tuning& t) {
+inline int elem_bytes(int kind) { return kind == kBatchGemvBF16 ? 2 : 4; }
+
+// Rows per tile: about tile_bytes of the matrix, a multiple of the block's
+// row groups (256 / lpr), at least one group.
+inline int64_t tile_rows(const BatchItem& it, const gb_batch_tuning& t) {
   const int64_t groups = kThreads / t.lanes_per_row;
-  const int64_t row_bytes = 4 * (n > 0 ? n : 1);
+  const int64_t row_bytes = elem_bytes(it.kind) * (it.n > 0 ? it.n : 1);
   int64_t r = (int64_t)t.tile_bytes / row_bytes;
   r = r / groups * groups;
   return r < groups ? groups : r;
 }
 
-inline bool active(int64_t m, int64_t n, float alpha) { return m > 0 && n > 0 && alpha != 0.f; }
+// Cost units of a tile: bytes it moves (GER reads and writes its rows).
+inline int64_t tile_cost(const BatchItem& it, int64_t rows) {
+  const int64_t row = it.kind == kBatchGerF32 ? 8 * it.n : elem_bytes(it.kind) * it.n;
+  return rows * (row + 8) + 4 * it.n + kTileOverhead;
+}
 
-inline int64_t count_tiles(int64_t count, const int64_t* m, const int64_t* n, const float* alpha,
-                           const gb_batch_tuning* table) {
+inline bool active(const BatchItem& it) { return it.m > 0 && it.n > 0 && it.alpha != 0.f; }
+
+inline bool shape_ok(const BatchItem& it) {
+  return it.m >= 0 && it.n >= 0 && it.m <= INT32_MAX && it.n <= INT32_MAX && it.reserved == 0 &&
+         it.reserved2 == 0 && (it.kind == kBatchGemvF32 || it.kind == kBatchGemvBF16 || it.kind == kBatchGerF32);
+}
+
+inline int64_t count_tiles(int64_t count, const BatchItem* items, const gb_batch_tuning* table) {
   int64_t T = 0;
   for (int64_t p = 0; p < count; ++p) {
-    if (!active(m[p], n[p], alpha ? alpha[p] : 1.f)) continue;
-    const int64_t R = tile_rows(n[p], table[bucket_of(n[p])]);
-    T += (m[p] + R - 1) / R;
+    if (!active(items[p])) continue;
+    const int64_t R = tile_rows(items[p], table[bucket_of(items[p].n)]);
+    T += (items[p].m + R - 1) / R;
   }
   return T;
 }
@@ -299,11 +424,151 @@ bool meets(const std::vector<Interval>& a, const std::vector<Interval>& b) {
 }
 
 }  // namespace
+
+size_t batch_plan_bytes(int64_t count, const BatchItem* items, const gb_batch_tuning* table) {
+  if (count < 0 || (count > 0 && !items)) return 0;
+  gb_batch_tuning def[GB_BATCH_BUCKETS];
+  if (!table) {
+    gb_sgemv_batch_default_tuning(def);
+    table = def;
+  }
+  for (int b = 0; b < GB_BATCH_BUCKETS; ++b)
+    if (!tuning_ok(table[b])) return 0;
+  for (int64_t p = 0; p < count; ++p)
+    if (!shape_ok(items[p])) return 0;
+  return (size_t)layout_of(count, count_tiles(count, items, table)).total;
+}
+
+int batch_plan(int64_t count, const BatchItem* items, const gb_batch_tuning* table, void* plan,
+               size_t plan_bytes) {
+  if (count < 0) return -1;
+  gb_batch_tuning def[GB_BATCH_BUCKETS];
+  if (!table) {
+    gb_sgemv_batch_default_tuning(def);
+    table = def;
+  }
+  for (int b = 0; b < GB_BATCH_BUCKETS; ++b)
+    if (!tuning_ok(table[b])) return -9;
+  std::vector<Interval> outs, ins;
+  for (int64_t p = 0; p < count; ++p) {
+    const BatchItem& it = items[p];
+    if (it.m < 0 || it.m > INT32_MAX) return -2;
+    if (!shape_ok(it)) return -3;
+    if (it.lda < (it.n > 1 ? it.n : 1)) return -4;
+    if (!active(it)) continue;
+    if (!it.A) return -6;
+    if (!it.x) return -7;
+    if (!it.c) return -8;
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(it.A);
+    const uintptr_t x0 = reinterpret_cast<uintptr_t>(it.x);
+    const uintptr_t c0 = reinterpret_cast<uintptr_t>(it.c);
+    const unsigned __int128 ab =
+        ((unsigned __int128)(it.m - 1) * (uint64_t)it.lda + (uint64_t)it.n) * (unsigned)elem_bytes(it.kind);
+    if (ab > (unsigned __int128)(UINTPTR_MAX - a0)) return -4;  // the matrix would run past the address space
+    const Interval a{a0, a0 + (uintptr_t)ab}, x{x0, x0 + (uintptr_t)(it.n * 4)}, c{c0, c0 + (uintptr_t)(it.m * 4)};
+    if (it.kind == kBatchGerF32) {  // writes C, reads x and y
+      outs.push_back(a);
+      ins.push_back(x);
+      ins.push_back(c);
+    } else {                        // writes c, reads A and x
+      outs.push_back(c);
+      ins.push_back(a);
+      ins.push_back(x);
+    }
+  }
+  auto by_lo = [](const Interval& a, const Interval& b) { return a.lo < b.lo; };
+  std::sort(outs.begin(), outs.end(), by_lo);
+  for (size_t i = 1; i < outs.size(); ++i)
+    if (outs[i].lo < outs[i - 1].hi) return -8;  // two problems write the same memory
+  std::sort(ins.begin(), ins.end(), by_lo);
+  if (meets(outs, ins)) return -8;               // an output overlaps some input
+  if (!plan || !aligned16(plan)) return -10;
+
+  const int64_t T = count_tiles(count, items, table);
+  const Layout L = layout_of(count, T);
+  if (plan_bytes < (size_t)L.total) return -11;
+  unsigned char* base = static_cast<unsigned char*>(plan);
+  std::memset(base, 0, (size_t)L.total);
+  BatchHeader* h = reinterpret_cast<BatchHeader*>(base);
+  BatchProblem* probs = reinterpret_cast<BatchProblem*>(base + L.problems);
+  BatchTile* tiles = reinterpret_cast<BatchTile*>(base + L.tiles);
+  int64_t* prefix = reinterpret_cast<int64_t*>(base + L.prefix);
+  int64_t t = 0, cost = 0;
+  for (int64_t p = 0; p < count; ++p) {
+    const BatchItem& it = items[p];
+    const int eb = elem_bytes(it.kind);
+    BatchProblem& pb = probs[p];
+    pb.A = it.A;
+    pb.x = it.x;
+    pb.c = it.c;
+    pb.lda = it.lda;
+    pb.m = (int32_t)it.m;
+    pb.n = (int32_t)it.n;
+    pb.alpha = it.alpha;
+    pb.kind = (uint8_t)it.kind;
+    pb.vec = aligned16(it.A) && aligned16(it.x) && (it.lda * eb) % 16 == 0;
+    if (!active(it)) continue;
+    const gb_batch_tuning& tu = table[bucket_of(it.n)];
+    const int64_t R = tile_rows(it, tu);
+    for (int64_t r0 = 0; r0 < it.m; r0 += R) {
+      BatchTile& tl = tiles[t];
+      tl.A = static_cast<const unsigned char*>(it.A) + r0 * it.lda * eb;
+      tl.x = it.x;
+      tl.c = it.c + r0;
+      tl.lda = it.lda;
+      tl.rows = (int32_t)std::min<int64_t>(R, it.m - r0);
+      tl.n = (int32_t)it.n;
+      tl.alpha = it.alpha;
+      tl.lpr_log2 = (uint8_t)log2_exact(tu.lanes_per_row);
+      tl.u_log2 = (uint8_t)log2_exact(tu.packs_per_iter);
+      tl.vec = pb.vec;
+      tl.kind = pb.kind;
+      prefix[t] = cost;
+      cost += tile_cost(it, tl.rows);
+      ++t;
+    }
+  }
+  prefix[T] = cost;
+  h->magic = kPlanMagic;
+  h->version = kPlanVersion;
+  h->count = count;
+  h->tiles = T;
+  h->total_cost = cost;
+  h->off_problems = L.problems;
+  h->off_tiles = L.tiles;
+  h->off_prefix = L.prefix;
+  return GB_OK;
+}
+
 }  // namespace gb
 
 // ------------------------------------------------------------------ C ABI ---
 
 using namespace gb;
+
+namespace {
+
+// FP32 GEMV problems of the public entry points as batch items.
+std::vector<BatchItem> sgemv_items(int64_t count, const int64_t* m, const int64_t* n, const int64_t* lda,
+                                   const float* alpha, const float* const* A, const float* const* x,
+                                   float* const* c) {
+  std::vector<BatchItem> items((size_t)count);
+  for (int64_t p = 0; p < count; ++p) {
+    BatchItem& it = items[(size_t)p];
+    it = BatchItem{};
+    it.kind = kBatchGemvF32;
+    it.m = m[p];
+    it.n = n[p];
+    it.lda = lda ? lda[p] : (n[p] > 1 ? n[p] : 1);
+    it.alpha = alpha ? alpha[p] : 1.f;
+    it.A = A ? const_cast<float*>(A[p]) : nullptr;
+    it.x = x ? x[p] : nullptr;
+    it.c = c ? c[p] : nullptr;
+  }
+  return items;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -322,16 +587,8 @@ void gb_sgemv_batch_default_tuning(gb_batch_tuning* table) {
 size_t gb_sgemv_batch_plan_bytes(int64_t count, const int64_t* m, const int64_t* n, const float* alpha,
                                  const gb_batch_tuning* table) {
   if (count < 0 || (count > 0 && (!m || !n))) return 0;
-  gb_batch_tuning def[GB_BATCH_BUCKETS];
-  if (!table) {
-    gb_sgemv_batch_default_tuning(def);
-    table = def;
-  }
-  for (int b = 0; b < GB_BATCH_BUCKETS; ++b)
-    if (!tuning_ok(table[b])) return 0;
-  for (int64_t p = 0; p < count; ++p)
-    if (m[p] < 0 || n[p] < 0 || m[p] > INT32_MAX || n[p] > INT32_MAX) return 0;
-  return (size_t)layout_of(count, count_tiles(count, m, n, alpha, table)).total;
+  const std::vector<BatchItem> items = sgemv_items(count, m, n, nullptr, alpha, nullptr, nullptr, nullptr);
+  return batch_plan_bytes(count, items.data(), table);
 }
 
 int gb_sgemv_batch_plan(int64_t count, const int64_t* m, const int64_t* n, const int64_t* lda,
@@ -347,89 +604,28 @@ int gb_sgemv_batch_plan(int64_t count, const int64_t* m, const int64_t* n, const
     if (!x) return -7;
     return -8;
   }
-  gb_batch_tuning def[GB_BATCH_BUCKETS];
-  if (!table) {
-    gb_sgemv_batch_default_tuning(def);
-    table = def;
-  }
-  for (int b = 0; b < GB_BATCH_BUCKETS; ++b)
-    if (!tuning_ok(table[b])) return -9;
-  std::vector<Interval> outs, ins;
-  for (int64_t p = 0; p < count; ++p) {
+  for (int64_t p = 0; p < count; ++p) {  // m is checked before n, as the argument order goes
     if (m[p] < 0 || m[p] > INT32_MAX) return -2;
     if (n[p] < 0 || n[p] > INT32_MAX) return -3;
-    if (lda[p] < (n[p] > 1 ? n[p] : 1)) return -4;
-    if (!active(m[p], n[p], alpha[p])) continue;
-    if (!A[p]) return -6;
-    if (!x[p]) return -7;
-    if (!c[p]) return -8;
-    const uintptr_t a0 = reinterpret_cast<uintptr_t>(A[p]);
-    const uintptr_t x0 = reinterpret_cast<uintptr_t>(x[p]);
-    const uintptr_t c0 = reinterpret_cast<uintptr_t>(c[p]);
-    const unsigned __int128 ab = ((unsigned __int128)(m[p] - 1) * (uint64_t)lda[p] + (uint64_t)n[p]) * 4u;
-    if (ab > (unsigned __int128)(UINTPTR_MAX - a0)) return -4;  // A would run past the address space
-    ins.push_back({a0, a0 + (uintptr_t)ab});
-    ins.push_back({x0, x0 + (uintptr_t)(n[p] * 4)});
-    outs.push_back({c0, c0 + (uintptr_t)(m[p] * 4)});
   }
-  auto by_lo = [](const Interval& a, const Interval& b) { return a.lo < b.lo; };
-  std::sort(outs.begin(), outs.end(), by_lo);
-  for (size_t i = 1; i < outs.size(); ++i)
-    if (outs[i].lo < outs[i - 1].hi) return -8;  // two problems write the same c
-  std::sort(ins.begin(), ins.end(), by_lo);
-  if (meets(outs, ins)) return -8;               // a c overlaps some A or x
-  if (!plan || !aligned16(plan)) return -10;
+  const std::vector<BatchItem> items = sgemv_items(count, m, n, lda, alpha, A, x, c);
+  return batch_plan(count, items.data(), table, plan, plan_bytes);
+}
 
-  const int64_t T = count_tiles(count, m, n, alpha, table);
-  const Layout L = layout_of(count, T);
-  if (plan_bytes < (size_t)L.total) return -11;
-  unsigned char* base = static_cast<unsigned char*>(plan);
-  std::memset(base, 0, (size_t)L.total);
-  BatchHeader* h = reinterpret_cast<BatchHeader*>(base);
-  BatchProblem* probs = reinterpret_cast<BatchProblem*>(base + L.problems);
-  BatchTile* tiles = reinterpret_cast<BatchTile*>(base + L.tiles);
-  int64_t* prefix = reinterpret_cast<int64_t*>(base + L.prefix);
-  int64_t t = 0, cost = 0;
-  for (int64_t p = 0; p < count; ++p) {
-    BatchProblem& pb = probs[p];
-    pb.A = A[p];
-    pb.x = x[p];
-    pb.c = c[p];
-    pb.lda = lda[p];
-    pb.m = (int32_t)m[p];
-    pb.n = (int32_t)n[p];
-    pb.alpha = alpha[p];
-    pb.vec = aligned16(A[p]) && aligned16(x[p]) && lda[p] % 4 == 0;
-    if (!active(m[p], n[p], alpha[p])) continue;
-    const gb_batch_tuning& tu = table[bucket_of(n[p])];
-    const int64_t R = tile_rows(n[p], tu);
-    for (int64_t r0 = 0; r0 < m[p]; r0 += R) {
-      BatchTile& tl = tiles[t];
-      tl.A = A[p] + r0 * lda[p];
-      tl.x = x[p];
-      tl.c = c[p] + r0;
-      tl.lda = lda[p];
-      tl.rows = (int32_t)std::min<int64_t>(R, m[p] - r0);
-      tl.n = (int32_t)n[p];
-      tl.alpha = alpha[p];
-      tl.lpr_log2 = (uint8_t)log2_exact(tu.lanes_per_row);
-      tl.u_log2 = (uint8_t)log2_exact(tu.packs_per_iter);
-      tl.vec = (uint8_t)pb.vec;
-      prefix[t] = cost;
-      cost += (int64_t)tl.rows * (4 * n[p] + 8) + 4 * n[p] + kTileOverhead;
-      ++t;
-    }
-  }
-  prefix[T] = cost;
-  h->magic = kPlanMagic;
-  h->version = kPlanVersion;
-  h->count = count;
-  h->tiles = T;
-  h->total_cost = cost;
-  h->off_problems = L.problems;
-  h->off_tiles = L.tiles;
-  h->off_prefix = L.prefix;
-  return GB_OK;
+size_t gb_batch_plan_bytes(int64_t count, const gb_batch_item* items, const gb_batch_tuning* table) {
+  return batch_plan_bytes(count, items, table);
+}
+
+int gb_batch_plan(int64_t count, const gb_batch_item* items, const gb_batch_tuning* table, void* plan,
+                  size_t plan_bytes) {
+  if (count < 0) return -1;
+  if (count > 0 && !items) return -2;
+  const int st = batch_plan(count, items, table, plan, plan_bytes);
+  if (st >= 0) return st;
+  if (st == -9) return -3;
+  if (st == -10) return -4;
+  if (st == -11) return -5;
+  return -2;
 }
 
 int gb_sgemv_batch(const void* plan_host, const void* plan_dev, gb_stream stream) {

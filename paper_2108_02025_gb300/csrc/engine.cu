@@ -1,0 +1,694 @@
+// Serving engine: continuous batching of GEMV / DOT / GER requests on one
+// GPU under an HBM budget (include/gbserve.h).  Not part of the paper, whose
+// operations run one call at a time (Sec. 4); a step launches one operand
+// generator and one batched level-2 kernel (batch.cu) for all its requests.
+//
+// One worker thread owns the device side: it admits arrived requests in
+// arrival order while the arena and the in-flight cap allow, launches the
+// admitted ones as a step on a free stream, and retires steps whose event
+// has completed.  Submission and polling only touch mutex-guarded queues.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "gbblas.h"
+#include "gbserve.h"
+#include "gb_internal.h"
+
+namespace gb {
+namespace {
+
+// ------------------------------------------------------------- generator ---
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) used as a counter hash.
+
+constexpr uint64_t kG = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kM1 = 0xBF58476D1CE4E5B9ull;
+constexpr uint64_t kM2 = 0x94D049BB133111EBull;
+constexpr uint64_t kS = 0xD1B54A32D192ED03ull;
+
+__host__ __device__ inline uint64_t sm_mix(uint64_t z) {
+  z ^= z >> 30;
+  z *= kM1;
+  z ^= z >> 27;
+  z *= kM2;
+  return z ^ (z >> 31);
+}
+
+inline uint64_t stream_key(uint64_t seed, uint64_t stream) { return sm_mix(sm_mix(seed + kG) ^ (stream * kS)); }
+
+enum FillKind : int32_t { kFillF32 = 0, kFillBF16 = 1 };
+
+struct FillSeg {  // 32 bytes
+  void* dst;
+  int64_t count;  // elements
+  uint64_t key;
+  int32_t kind, pad;
+};
+static_assert(sizeof(FillSeg) == 32, "fill segment layout");
+
+constexpr int64_t kFillChunk = 16384;  // elements per block
+
+// Block b fills chunk b - first[s] of segment s, the last s with first[s] <= b.
+__global__ void __launch_bounds__(kThreads) fill_kernel(const FillSeg* __restrict__ segs,
+                                                        const int64_t* __restrict__ first, int nseg) {
+  const int64_t b = blockIdx.x;
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const FillSeg sg = segs[lo];
+  const int64_t e0 = (b - first[lo]) * kFillChunk;
+  const int64_t e1 = e0 + kFillChunk < sg.count ? e0 + kFillChunk : sg.count;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
+    const uint64_t u = sm_mix(sg.key + (uint64_t)(e + 1) * kG);
+    const float v = __fsub_rn(__fmul_rn((float)(uint32_t)(u >> 40), 0x1p-23f), 1.0f);
+    if (sg.kind == kFillF32) {
+      static_cast<float*>(sg.dst)[e] = v;
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      static_cast<uint16_t*>(sg.dst)[e] = *reinterpret_cast<const uint16_t*>(&h);
+    }
+  }
+}
+
+// ----------------------------------------------------------------- arena ---
+
+constexpr size_t kAlign = 256;
+
+inline size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// First-fit allocator over [0, cap) with coalescing free ranges.
+class Arena {
+ public:
+  void init(size_t cap) {
+    cap_ = cap;
+    free_.clear();
+    free_[0] = cap;
+    used_ = peak_ = 0;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = round_up(bytes, kAlign);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      *off = it->first;
+      const size_t rest = it->second - bytes;
+      const size_t at = it->first + bytes;
+      free_.erase(it);
+      if (rest) free_[at] = rest;
+      used_ += bytes;
+      peak_ = std::max(peak_, used_);
+      return true;
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = round_up(bytes, kAlign);
+    used_ -= bytes;
+    auto next = free_.lower_bound(off);
+    size_t start = off, len = bytes;
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == off) {
+        start = prev->first;
+        len += prev->second;
+        free_.erase(prev);
+      }
+    }
+    if (next != free_.end() && off + bytes == next->first) {
+      len += next->second;
+      free_.erase(next);
+    }
+    free_[start] = len;
+  }
+  size_t used() const { return used_; }
+  size_t peak() const { return peak_; }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t cap_ = 0, used_ = 0, peak_ = 0;
+};
+
+// -------------------------------------------------------------- requests ---
+
+struct Piece {
+  size_t off, bytes;  // inside the request's range
+};
+
+// Layout of a request's operands: leading dimensions and 256-byte pieces.
+struct Footprint {
+  int64_t ld = 0;
+  Piece p[3] = {};  // GEMV: A|Q, x, c; DOT: x, y, alpha; GER: C, x, y
+  int pieces = 0;
+  size_t total = 0;
+};
+
+inline bool request_ok(const gb_request& r) {
+  if (r.reserved != 0) return false;
+  if (r.n < 1 || r.n > INT32_MAX) return false;
+  switch (r.op) {
+    case GB_REQ_GEMV:
+      return (r.form == GB_FORM_F32 || r.form == GB_FORM_BF16) && r.m >= 1 && r.m <= INT32_MAX;
+    case GB_REQ_GER:
+      return r.form == GB_FORM_F32 && r.m >= 1 && r.m <= INT32_MAX;
+    case GB_REQ_DOT:
+      return r.form == GB_FORM_F32;
+    default:
+      return false;
+  }
+}
+
+Footprint footprint(const gb_request& r) {
+  Footprint f;
+  auto add = [&](size_t bytes) {
+    f.p[f.pieces++] = Piece{f.total, bytes};
+    f.total += round_up(bytes > 0 ? bytes : 1, kAlign);
+  };
+  const size_t m = (size_t)r.m, n = (size_t)r.n;
+  if (r.op == GB_REQ_GEMV) {
+    if (r.form == GB_FORM_BF16) {
+      f.ld = (int64_t)round_up(n, 8);
+      add(m * (size_t)f.ld * 2);
+    } else {
+      f.ld = (int64_t)round_up(n, 4);
+      add(m * (size_t)f.ld * 4);
+    }
+    add(n * 4);
+    add(m * 4);
+  } else if (r.op == GB_REQ_DOT) {
+    f.ld = (int64_t)round_up(n, 4);
+    add((size_t)f.ld * 4);  // x, stored as the one row of a GEMV
+    add(n * 4);
+    add(4);
+  } else {
+    f.ld = (int64_t)round_up(n, 4);
+    add(m * (size_t)f.ld * 4);
+    add(m * 4);
+    add(n * 4);
+  }
+  return f;
+}
+
+struct Req {
+  gb_request r;
+  Footprint f;
+  size_t off = 0;
+  unsigned char* base = nullptr;  // device address of the range (host-only: nullptr)
+  int64_t admit_ns = 0, launch_ns = 0, done_ns = 0, step = -1;
+  int status = GB_OK;
+  unsigned char* ptr(int i) const { return base + f.p[i].off; }
+};
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+// ------------------------------------------------------------------ slots ---
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  unsigned char* host = nullptr;  // pinned staging of the step's descriptors
+  unsigned char* dev = nullptr;
+  size_t cap = 0;
+  bool busy = false;
+  int64_t index = -1;
+  int64_t sim_done_ns = 0;  // host-only mode
+  bool failed = false;
+  int fail_status = GB_OK;
+  std::vector<Req*> reqs;
+};
+
+}  // namespace
+}  // namespace gb
+
+using namespace gb;
+
+struct gb_engine {
+  gb_engine_config cfg{};
+  gb_batch_tuning table[GB_BATCH_BUCKETS];
+  bool host_only = false;
+  unsigned char* arena_base = nullptr;
+  Arena arena;
+  std::vector<Slot> slots;
+
+  std::mutex mu;  // guards pending, done, counters, stop
+  std::condition_variable cv_work, cv_done;
+  std::deque<Req*> pending;  // sorted by arrival
+  std::deque<gb_completion> done;
+  bool stop = false;
+  int64_t submitted = 0, completed = 0, failed = 0;
+
+  // worker-only state
+  std::deque<Req*> admitted;
+  int64_t inflight = 0, inflight_peak = 0, steps = 0, steps_inflight_peak = 0;
+  std::atomic<int64_t> admitted_count{0};
+  std::atomic<size_t> bytes_in_use{0}, bytes_peak{0};
+  std::thread worker;
+
+  void run();
+  bool retire();
+  bool admit();
+  bool launch();
+  int launch_step(Slot& s, std::vector<Req*>& reqs);
+  int ensure_capacity(Slot& s, size_t bytes);
+  void finish(Slot& s, int64_t t, int status);
+};
+
+// Retire every step whose work has completed.
+bool gb_engine::retire() {
+  bool any = false;
+  for (Slot& s : slots) {
+    if (!s.busy) continue;
+    int status = GB_OK;
+    if (s.failed) {
+      status = s.fail_status;
+    } else if (host_only) {
+      if (now_ns() < s.sim_done_ns) continue;
+    } else {
+      const cudaError_t q = cudaEventQuery(s.done);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) {
+        cudaGetLastError();
+        status = GB_ERR_CUDA;
+      }
+    }
+    finish(s, now_ns(), status);
+    any = true;
+  }
+  return any;
+}
+
+void gb_engine::finish(Slot& s, int64_t t, int status) {
+  std::vector<gb_completion> out;
+  out.reserve(s.reqs.size());
+  for (Req* q : s.reqs) {
+    q->done_ns = t;
+    arena.release(q->off, q->f.total);
+    gb_completion c{};
+    c.id = q->r.id;
+    c.status = status;
+    c.op = q->r.op;
+    c.arrival_ns = q->r.arrival_ns;
+    c.admitted_ns = q->admit_ns;
+    c.launched_ns = q->launch_ns;
+    c.done_ns = t;
+    c.step = s.index;
+    c.bytes = (int64_t)q->f.total;
+    out.push_back(c);
+    delete q;
+  }
+  inflight -= (int64_t)s.reqs.size();
+  s.reqs.clear();
+  s.busy = false;
+  s.failed = false;
+  bytes_in_use = arena.used();
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (const gb_completion& c : out) {
+      done.push_back(c);
+      ++completed;
+      if (c.status != GB_OK) ++failed;
+    }
+  }
+  cv_done.notify_all();
+}
+
+// Admit arrived requests in arrival order while memory and the cap allow.
+bool gb_engine::admit() {
+  bool any = false;
+  const int64_t t = now_ns();
+  std::lock_guard<std::mutex> lk(mu);
+  while (!pending.empty()) {
+    Req* q = pending.front();
+    if ((q->r.arrival_ns > t && !stop) || inflight >= cfg.max_inflight) break;
+    size_t off = 0;
+    if (!arena.alloc(q->f.total, &off)) break;  // head of line waits for memory
+    q->off = off;
+    q->base = host_only ? nullptr : arena_base + off;
+    q->admit_ns = t;
+    admitted.push_back(q);
+    pending.pop_front();
+    ++inflight;
+    ++admitted_count;
+    inflight_peak = std::max(inflight_peak, inflight);
+    any = true;
+  }
+  bytes_in_use = arena.used();
+  bytes_peak = arena.peak();
+  return any;
+}
+
+int gb_engine::ensure_capacity(Slot& s, size_t bytes) {
+  if (bytes <= s.cap) return GB_OK;
+  const size_t cap = round_up(std::max(bytes, 2 * s.cap), 1 << 16);
+  if (s.host) cudaFreeHost(s.host);
+  if (s.dev) cudaFree(s.dev);
+  s.host = nullptr;
+  s.dev = nullptr;
+  s.cap = 0;
+  if (cudaHostAlloc(&s.host, cap, cudaHostAllocDefault) != cudaSuccess) return GB_ERR_CUDA;
+  if (cudaMalloc(&s.dev, cap) != cudaSuccess) return GB_ERR_CUDA;
+  s.cap = cap;
+  return GB_OK;
+}
+
+// Enqueue one step: descriptors, operand fill, one batched launch for every
+// request, result copies, event.
+int gb_engine::launch_step(Slot& s, std::vector<Req*>& reqs) {
+  // operand segments (inputs only; outputs of GER/GEMV/DOT are inputs too)
+  std::vector<FillSeg> segs;
+  for (Req* q : reqs) {
+    const gb_request& r = q->r;
+    const uint64_t seed = r.seed;
+    if (r.op == GB_REQ_GEMV) {
+      const int kind = r.form == GB_FORM_BF16 ? kFillBF16 : kFillF32;
+      segs.push_back({q->ptr(0), r.m * q->f.ld, stream_key(seed, 1), kind, 0});
+      segs.push_back({q->ptr(1), r.n, stream_key(seed, 2), kFillF32, 0});
+      segs.push_back({q->ptr(2), r.m, stream_key(seed, 3), kFillF32, 0});
+    } else if (r.op == GB_REQ_DOT) {
+      segs.push_back({q->ptr(0), r.n, stream_key(seed, 1), kFillF32, 0});
+      segs.push_back({q->ptr(1), r.n, stream_key(seed, 2), kFillF32, 0});
+      segs.push_back({q->ptr(2), 1, stream_key(seed, 3), kFillF32, 0});
+    } else {
+      segs.push_back({q->ptr(0), r.m * q->f.ld, stream_key(seed, 1), kFillF32, 0});
+      segs.push_back({q->ptr(1), r.m, stream_key(seed, 2), kFillF32, 0});
+      segs.push_back({q->ptr(2), r.n, stream_key(seed, 3), kFillF32, 0});
+    }
+  }
+  std::vector<int64_t> first(segs.size() + 1, 0);
+  for (size_t i = 0; i < segs.size(); ++i)
+    first[i + 1] = first[i] + (segs[i].count + kFillChunk - 1) / kFillChunk;
+
+  // every request's compute in one batched launch: GEMVs (FP32 or BF16 A),
+  // DOTs as one-row FP32 GEMVs, GERs
+  std::vector<BatchItem> items;
+  items.reserve(reqs.size());
+  for (Req* q : reqs) {
+    const gb_request& r = q->r;
+    BatchItem it{};
+    it.n = r.n;
+    it.lda = q->f.ld;
+    if (r.op == GB_REQ_GEMV) {
+      it.kind = r.form == GB_FORM_BF16 ? kBatchGemvBF16 : kBatchGemvF32;
+      it.m = r.m;
+      it.alpha = r.alpha;
+      it.A = q->ptr(0);
+      it.x = reinterpret_cast<const float*>(q->ptr(1));
+      it.c = reinterpret_cast<float*>(q->ptr(2));
+    } else if (r.op == GB_REQ_DOT) {
+      it.kind = kBatchGemvF32;
+      it.m = 1;
+      it.alpha = 1.0f;
+      it.A = q->ptr(0);
+      it.x = reinterpret_cast<const float*>(q->ptr(1));
+      it.c = reinterpret_cast<float*>(q->ptr(2));
+    } else {
+      it.kind = kBatchGerF32;
+      it.m = r.m;
+      it.alpha = r.alpha;
+      it.A = q->ptr(0);                                    // C
+      it.x = reinterpret_cast<const float*>(q->ptr(2));  // y
+      it.c = reinterpret_cast<float*>(q->ptr(1));        // x
+    }
+    items.push_back(it);
+  }
+  const int64_t nb = (int64_t)items.size();
+  const size_t plan_bytes = batch_plan_bytes(nb, items.data(), table);
+  if (plan_bytes == 0) return GB_ERR_UNSUPPORTED;
+
+  // staging layout: segs | first | plan
+  const size_t o_first = round_up(segs.size() * sizeof(FillSeg), 16);
+  const size_t o_plan = round_up(o_first + first.size() * sizeof(int64_t), 256);
+  const size_t total = o_plan + plan_bytes;
+  int st = ensure_capacity(s, total);
+  if (st != GB_OK) return st;
+  std::memcpy(s.host, segs.data(), segs.size() * sizeof(FillSeg));
+  std::memcpy(s.host + o_first, first.data(), first.size() * sizeof(int64_t));
+  st = batch_plan(nb, items.data(), table, s.host + o_plan, plan_bytes);
+  if (st != GB_OK) return GB_ERR_UNSUPPORTED;
+  cudaStream_t sm = s.stream;
+  if (cudaMemcpyAsync(s.dev, s.host, total, cudaMemcpyHostToDevice, sm) != cudaSuccess) return GB_ERR_CUDA;
+  if (!segs.empty()) {
+    const int64_t blocks = first.back();
+    fill_kernel<<<(unsigned)blocks, kThreads, 0, sm>>>(reinterpret_cast<const FillSeg*>(s.dev),
+                                                       reinterpret_cast<const int64_t*>(s.dev + o_first),
+                                                       (int)segs.size());
+    if (cudaPeekAtLastError() != cudaSuccess) return GB_ERR_CUDA;
+  }
+  if (gb_sgemv_batch(s.host + o_plan, s.dev + o_plan, sm) != GB_OK) return GB_ERR_CUDA;
+  for (Req* q : reqs) {
+    const gb_request& r = q->r;
+    if (!r.out) continue;
+    cudaError_t e;
+    if (r.op == GB_REQ_GER)
+      e = cudaMemcpy2DAsync(r.out, (size_t)r.n * 4, q->ptr(0), (size_t)q->f.ld * 4, (size_t)r.n * 4, (size_t)r.m,
+                            cudaMemcpyDeviceToHost, sm);
+    else
+      e = cudaMemcpyAsync(r.out, q->ptr(2), r.op == GB_REQ_DOT ? 4 : (size_t)r.m * 4, cudaMemcpyDeviceToHost, sm);
+    if (e != cudaSuccess) return GB_ERR_CUDA;
+  }
+  if (cudaEventRecord(s.done, sm) != cudaSuccess) return GB_ERR_CUDA;
+  return GB_OK;
+}
+
+// Launch the admitted requests as a step on a free slot.
+bool gb_engine::launch() {
+  if (admitted.empty()) return false;
+  Slot* s = nullptr;
+  int busy = 0;
+  for (Slot& x : slots) {
+    if (x.busy) ++busy;
+    else if (!s) s = &x;
+  }
+  if (!s) return false;
+  const size_t k = std::min(admitted.size(), (size_t)cfg.max_step_requests);
+  s->reqs.assign(admitted.begin(), admitted.begin() + (long)k);
+  admitted.erase(admitted.begin(), admitted.begin() + (long)k);
+  s->index = steps++;
+  s->busy = true;
+  steps_inflight_peak = std::max<int64_t>(steps_inflight_peak, busy + 1);
+  const int64_t t = now_ns();
+  size_t bytes = 0;
+  for (Req* q : s->reqs) {
+    q->launch_ns = t;
+    q->step = s->index;
+    bytes += q->f.total;
+  }
+  if (fault_injected(kInjectStep)) {
+    s->failed = true;
+    s->fail_status = GB_ERR_INJECTED;
+    return true;
+  }
+  if (host_only) {
+    s->sim_done_ns = t + (int64_t)((double)bytes / cfg.sim_bytes_per_ns);
+    return true;
+  }
+  const int st = launch_step(*s, s->reqs);
+  if (st != GB_OK) {
+    // nothing more is enqueued on this stream; let what was enqueued finish
+    cudaStreamSynchronize(s->stream);
+    cudaGetLastError();
+    s->failed = true;
+    s->fail_status = st == GB_ERR_CUDA ? GB_ERR_CUDA : st;
+  }
+  return true;
+}
+
+void gb_engine::run() {
+  for (;;) {
+    bool progress = retire();
+    progress |= admit();
+    progress |= launch();
+    bool busy = false;
+    for (const Slot& s : slots) busy |= s.busy;
+    std::unique_lock<std::mutex> lk(mu);
+    if (stop && pending.empty() && admitted.empty() && !busy) break;
+    if (progress) continue;
+    if (busy) {  // steps on the GPU: poll their events again shortly
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(5));
+      continue;
+    }
+    // idle: sleep until the next arrival or a submission
+    if (!pending.empty()) {
+      const int64_t wait = pending.front()->r.arrival_ns - now_ns();
+      if (wait > 0) cv_work.wait_for(lk, std::chrono::nanoseconds(std::min<int64_t>(wait, 1000000)));
+    } else if (!stop) {
+      cv_work.wait_for(lk, std::chrono::milliseconds(1));
+    }
+  }
+}
+
+extern "C" {
+
+int64_t gb_engine_now_ns(void) { return now_ns(); }
+
+size_t gb_engine_request_bytes(const gb_request* r) {
+  if (!r || !request_ok(*r)) return 0;
+  return footprint(*r).total;
+}
+
+int gb_engine_create(const gb_engine_config* cfg, gb_engine** out) {
+  if (!cfg) return -1;
+  if (!out) return -2;
+  *out = nullptr;
+  if (cfg->budget_bytes < ((size_t)1 << 20) || cfg->streams < 1 || cfg->streams > 16 ||
+      cfg->max_inflight < 1 || cfg->max_step_requests < 1 || (cfg->flags & ~GB_ENGINE_HOST_ONLY) != 0)
+    return -1;
+  const bool host_only = (cfg->flags & GB_ENGINE_HOST_ONLY) != 0;
+  if (host_only && !(cfg->sim_bytes_per_ns > 0.0)) return -1;
+  gb_engine* e = new gb_engine();
+  e->cfg = *cfg;
+  e->host_only = host_only;
+  if (cfg->table) std::memcpy(e->table, cfg->table, sizeof(e->table));
+  else gb_sgemv_batch_default_tuning(e->table);
+  e->cfg.table = e->table;
+  {  // validate the table with a one-problem plan size
+    const int64_t one = 1;
+    const float a = 1.f;
+    if (gb_sgemv_batch_plan_bytes(1, &one, &one, &a, e->table) == 0) {
+      delete e;
+      return -1;
+    }
+  }
+  e->arena.init(cfg->budget_bytes);
+  e->slots.resize((size_t)cfg->streams);
+  if (!host_only) {
+    bool ok = cudaMalloc(&e->arena_base, cfg->budget_bytes) == cudaSuccess;
+    for (Slot& s : e->slots) {
+      if (!ok) break;
+      ok = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+      cudaGetLastError();
+      for (Slot& s : e->slots) {
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.stream) cudaStreamDestroy(s.stream);
+      }
+      if (e->arena_base) cudaFree(e->arena_base);
+      delete e;
+      return GB_ERR_CUDA;
+    }
+  }
+  int dev = 0;
+  if (!host_only) cudaGetDevice(&dev);
+  try {
+    e->worker = std::thread([e, dev, host_only] {
+      if (!host_only) cudaSetDevice(dev);
+      e->run();
+    });
+  } catch (...) {
+    for (Slot& s : e->slots) {
+      if (s.done) cudaEventDestroy(s.done);
+      if (s.stream) cudaStreamDestroy(s.stream);
+    }
+    if (e->arena_base) cudaFree(e->arena_base);
+    delete e;
+    return GB_ERR_CUDA;
+  }
+  *out = e;
+  return GB_OK;
+}
+
+int gb_engine_submit(gb_engine* e, const gb_request* r) {
+  if (!e) return -1;
+  if (!r || !request_ok(*r)) return -2;
+  if (r->out && !e->host_only) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, r->out) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+      cudaGetLastError();
+      return -2;
+    }
+  }
+  Req* q = new Req();
+  q->r = *r;
+  q->f = footprint(*r);
+  if (q->f.total > e->cfg.budget_bytes) {
+    delete q;
+    return GB_ERR_BUDGET;
+  }
+  if (q->r.arrival_ns == 0) q->r.arrival_ns = now_ns();
+  {
+    std::lock_guard<std::mutex> lk(e->mu);
+    auto pos = std::upper_bound(e->pending.begin(), e->pending.end(), q->r.arrival_ns,
+                                [](int64_t t, const Req* x) { return t < x->r.arrival_ns; });
+    e->pending.insert(pos, q);
+    ++e->submitted;
+  }
+  e->cv_work.notify_one();
+  return GB_OK;
+}
+
+int gb_engine_poll(gb_engine* e, gb_completion* out, int max) {
+  if (!e || max < 0 || (max > 0 && !out)) return -1;
+  std::lock_guard<std::mutex> lk(e->mu);
+  int k = 0;
+  while (k < max && !e->done.empty()) {
+    out[k++] = e->done.front();
+    e->done.pop_front();
+  }
+  return k;
+}
+
+int gb_engine_drain(gb_engine* e, int64_t timeout_ms) {
+  if (!e || timeout_ms < 0) return -1;
+  std::unique_lock<std::mutex> lk(e->mu);
+  const bool ok = e->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                                      [e] { return e->completed == e->submitted; });
+  return ok ? GB_OK : GB_ERR_TIMEOUT;
+}
+
+int gb_engine_stats_get(gb_engine* e, gb_engine_stats* out) {
+  if (!e || !out) return -1;
+  std::lock_guard<std::mutex> lk(e->mu);
+  out->submitted = e->submitted;
+  out->admitted = e->admitted_count.load();
+  out->completed = e->completed;
+  out->failed = e->failed;
+  out->steps = e->steps;
+  out->inflight_peak = e->inflight_peak;
+  out->steps_inflight_peak = e->steps_inflight_peak;
+  out->bytes_in_use = e->bytes_in_use.load();
+  out->bytes_peak = e->bytes_peak.load();
+  out->budget_bytes = e->cfg.budget_bytes;
+  return 0;
+}
+
+void gb_engine_destroy(gb_engine* e) {
+  if (!e) return;
+  gb_engine_drain(e, 60000);
+  {
+    std::lock_guard<std::mutex> lk(e->mu);
+    e->stop = true;
+  }
+  e->cv_work.notify_all();
+  if (e->worker.joinable()) e->worker.join();
+  for (Req* q : e->pending) delete q;
+  for (Slot& s : e->slots) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    for (Req* q : s.reqs) delete q;
+    if (s.done) cudaEventDestroy(s.done);
+    if (s.stream) cudaStreamDestroy(s.stream);
+    if (s.host) cudaFreeHost(s.host);
+    if (s.dev) cudaFree(s.dev);
+  }
+  for (Req* q : e->admitted) delete q;
+  if (e->arena_base) cudaFree(e->arena_base);
+  delete e;
+}
+
+}  // extern "C"

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "gb_split.h"
+#include "gbblas.h"
 
 namespace gb {
 
@@ -82,6 +83,24 @@ struct GerPlan {
 // Blocks to launch for `units` independent work units: every SM filled to
 // the kernel's occupancy, never more blocks than units.
 int grid_size(const void* kernel, int64_t units, size_t smem = 0);
+
+// Batched level-2 problems (batch.cu): gb_batch_item kinds, and the
+// planner behind gb_sgemv_batch_plan / gb_batch_plan with the statuses of
+// gb_sgemv_batch_plan (argument numbers of its FP32 form).
+constexpr int kBatchGemvF32 = GB_BATCH_GEMV_F32;
+constexpr int kBatchGemvBF16 = GB_BATCH_GEMV_BF16;
+constexpr int kBatchGerF32 = GB_BATCH_GER_F32;
+using BatchItem = gb_batch_item;
+size_t batch_plan_bytes(int64_t count, const BatchItem* items, const gb_batch_tuning* table);
+int batch_plan(int64_t count, const BatchItem* items, const gb_batch_tuning* table, void* plan,
+               size_t plan_bytes);
+
+// Host-side fault injection (GB_FAULT_INJECT=<site>:<k>): true on the k-th
+// call for that site.  Sites: the gb_op codes of gemv, dot, ger, and a step
+// of the serving engine.
+constexpr int kInjectStep = 3;
+constexpr int kInjectSites = 4;
+bool fault_injected(int site);
 
 // Allow `kernel` `bytes` of dynamic shared memory on the current device
 // (once per kernel and device).  Returns false if the device refuses.

@@ -19,10 +19,10 @@ HEADER = np.dtype([("magic", "<u4"), ("version", "<u4"), ("count", "<i8"), ("til
                    ("total", "<i8"), ("off_problems", "<i8"), ("off_tiles", "<i8"),
                    ("off_prefix", "<i8"), ("reserved", "<i8")])
 PROBLEM = np.dtype([("A", "<u8"), ("x", "<u8"), ("c", "<u8"), ("lda", "<i8"), ("m", "<i4"),
-                    ("n", "<i4"), ("alpha", "<f4"), ("vec", "<i4")])
+                    ("n", "<i4"), ("alpha", "<f4"), ("vec", "u1"), ("kind", "u1"), ("pad", "<u2")])
 TILE = np.dtype([("A", "<u8"), ("x", "<u8"), ("c", "<u8"), ("lda", "<i8"), ("rows", "<i4"),
                  ("n", "<i4"), ("alpha", "<f4"), ("lpr_log2", "u1"), ("u_log2", "u1"), ("vec", "u1"),
-                 ("pad", "u1")])
+                 ("kind", "u1")])
 
 
 def log_uniform(count, seed, stream, lo, hi):
@@ -123,7 +123,7 @@ def check_plan(fb, buf, table):
         assert np.array_equal(mine["A"], a_row0)
         assert np.all(mine["x"] == fb.x[p]) and np.all(mine["lda"] == fb.lda[p])
         assert np.all(mine["n"] == fb.n[p]) and np.all(mine["alpha"] == fb.alpha[p])
-        assert np.all(mine["vec"] == pr["vec"])
+        assert np.all(mine["vec"] == pr["vec"]) and np.all(mine["kind"] == 0) and pr["kind"] == 0
         e = table[bucket(int(fb.n[p]))]
         assert np.all(mine["lpr_log2"] == int(np.log2(e.lanes_per_row)))
         assert np.all(mine["u_log2"] == int(np.log2(e.packs_per_iter)))
@@ -246,3 +246,89 @@ def test_launch_rejects_a_non_plan_without_touching_the_device():
     assert st == gb.GB_OK
     assert gb.gb_sgemv_batch(buf, None, 0) == -2
     assert gb.gb_sgemv_batch(buf, (1 << 40) + 4, 0) == -2
+
+
+def items_of(specs, base=1 << 41):
+    """gb_batch_item array from (kind, m, n, lda, alpha) at fake disjoint addresses."""
+    arr = (gb.BatchItem * max(1, len(specs)))()
+    addr = base
+    for i, (kind, m, n, lda, alpha) in enumerate(specs):
+        eb = 2 if kind == gb.BATCH_GEMV_BF16 else 4
+        a = addr
+        addr += (m * lda * eb + 255) // 256 * 256 + 256
+        xx = addr
+        addr += (n * 4 + 255) // 256 * 256 + 256
+        cc = addr
+        addr += (m * 4 + 255) // 256 * 256 + 256
+        arr[i] = gb.BatchItem(kind, 0, m, n, lda, alpha, 0, a, xx, cc)
+    return arr
+
+
+def test_mixed_items_plan():
+    specs = [(gb.BATCH_GEMV_F32, 100, 40, 40, 1.0), (gb.BATCH_GEMV_BF16, 300, 1000, 1000, 0.5),
+             (gb.BATCH_GEMV_BF16, 7, 30, 30, 1.0), (gb.BATCH_GER_F32, 50, 64, 64, -1.0),
+             (gb.BATCH_GER_F32, 9, 10, 11, 2.0), (gb.BATCH_GEMV_F32, 5, 5, 5, 0.0)]
+    arr = items_of(specs)
+    table = gb.tuning_table()
+    nb = gb.gb_batch_plan_bytes(len(specs), arr, table)
+    buf = aligned_buffer(nb)
+    assert gb.gb_batch_plan(len(specs), arr, table, buf, nb) == gb.GB_OK
+    h, probs, raw, prefix = decode_raw(buf)
+    assert list(probs["kind"]) == [s[0] for s in specs]
+    # 16-byte path: lda * element bytes a multiple of 16 (aligned fake addresses)
+    assert list(probs["vec"]) == [1, 1, 0, 1, 0, 0]
+    kinds = []
+    for p, (kind, m, n, lda, alpha) in enumerate(specs):
+        inside = (raw["c"] >= np.uint64(arr[p].c)) & (raw["c"] < np.uint64(arr[p].c + 4 * m))
+        mine = raw[inside]
+        if alpha == 0:
+            assert mine.size == 0
+            continue
+        eb = 2 if kind == gb.BATCH_GEMV_BF16 else 4
+        row0 = (mine["c"] - arr[p].c) // 4
+        assert np.array_equal(mine["A"], arr[p].A + row0.astype(np.uint64) * np.uint64(lda * eb))
+        assert mine["rows"].sum() == m and np.all(mine["kind"] == kind)
+        kinds += [kind] * mine.size
+        # cost: rows * (row bytes moved + 8) + 4n + 256; GER moves its rows twice
+        row = (8 if kind == gb.BATCH_GER_F32 else eb) * n
+        idx = np.nonzero(inside)[0]
+        assert np.array_equal(np.diff(prefix)[idx], mine["rows"].astype(np.int64) * (row + 8) + 4 * n + 256)
+    assert len(kinds) == h["tiles"]
+
+
+def decode_raw(buf):
+    h = np.frombuffer(buf[:HEADER.itemsize].tobytes(), HEADER)[0]
+    probs = np.frombuffer(buf[h["off_problems"]:h["off_problems"] + h["count"] * PROBLEM.itemsize].tobytes(),
+                          PROBLEM)
+    raw = np.frombuffer(buf[h["off_tiles"]:h["off_tiles"] + h["tiles"] * TILE.itemsize].tobytes(), TILE)
+    prefix = np.frombuffer(buf[h["off_prefix"]:h["off_prefix"] + (h["tiles"] + 1) * 8].tobytes(), "<i8")
+    return h, probs, raw, prefix
+
+
+def test_mixed_items_argument_checks():
+    ok = [(gb.BATCH_GEMV_F32, 10, 10, 12, 1.0), (gb.BATCH_GER_F32, 10, 10, 12, 1.0)]
+    arr = items_of(ok)
+    nb = gb.gb_batch_plan_bytes(2, arr, None)
+    buf = aligned_buffer(nb + 16)
+    assert gb.gb_batch_plan(2, arr, None, buf, nb) == gb.GB_OK
+    assert gb.gb_batch_plan(-1, arr, None, buf, nb) == -1
+    assert gb.gb_batch_plan(2, None, None, buf, nb) == -2
+    for field, value in (("kind", 3), ("reserved", 1), ("reserved2", 1), ("m", -1), ("n", -2), ("lda", 9),
+                         ("A", 0), ("x", 0), ("c", 0)):
+        bad = items_of(ok)
+        setattr(bad[1], field, value)
+        assert gb.gb_batch_plan(2, bad, None, buf, nb) == -2, field
+    # GER: C written, x and y read; GEMV: c written, A and x read
+    bad = items_of(ok)
+    bad[1].c = bad[0].c          # GER's x is GEMV's output
+    assert gb.gb_batch_plan(2, bad, None, buf, nb) == -2
+    bad = items_of(ok)
+    bad[1].x = bad[1].A + 64     # GER's y inside its own C
+    assert gb.gb_batch_plan(2, bad, None, buf, nb) == -2
+    bad = items_of(ok)
+    bad[0].x = bad[1].x          # two readers of one vector are fine
+    assert gb.gb_batch_plan(2, bad, None, buf, nb) == gb.GB_OK
+    assert gb.gb_batch_plan(2, arr, gb.tuning_table({4: (4, 3, 65536)}), buf, nb) == -3
+    assert gb.gb_batch_plan(2, arr, None, buf[1:], nb) == -4
+    assert gb.gb_batch_plan(2, arr, None, buf, nb - 16) == -5
+    assert gb.gb_batch_plan_bytes(2, items_of([(7, 1, 1, 1, 1.0)] * 2), None) == 0

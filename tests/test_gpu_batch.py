@@ -159,3 +159,75 @@ def test_full_size_workload_sampled():
         assert rel_err(got, want, scale) <= TOL, (p, m, n)
     del wl, b
     torch.cuda.empty_cache()
+
+
+class Item:
+    """One gb_batch_item on the device, with its oracle."""
+
+    def __init__(self, kind, m, n, pad, alpha, seed, misalign=0):
+        self.kind, self.m, self.n, self.alpha = kind, m, n, alpha
+        self.ld = max(n + pad, 1)
+        size = (m - 1) * self.ld + n if m > 0 and n > 0 else 0
+        A = synth.uniform(size, seed, 1, np.float32)
+        if kind == gb.BATCH_GEMV_BF16:
+            self.codes = oracle.bf16_encode(A)
+            for r in range(m - 1):  # padding codes: NaN
+                self.codes[r * self.ld + n:(r + 1) * self.ld] = 0x7FC0
+            self.A = oracle.bf16_decode(self.codes)
+            self.dA = to_dev(self.codes.view(np.int16), misalign)
+        else:
+            for r in range(m - 1):
+                A[r * self.ld + n:(r + 1) * self.ld] = np.nan
+            self.A = A
+            self.dA = to_dev(A, misalign)
+        self.vec_n = synth.uniform(n, seed, 2, np.float32)
+        self.vec_m = synth.uniform(m, seed, 3, np.float32)
+        self.dx = to_dev(self.vec_n, misalign)
+        if kind == gb.BATCH_GER_F32:
+            self.dc = to_dev(self.vec_m, misalign)
+            self.out = None
+        else:
+            self.out = Guarded(self.vec_m, misalign)
+            self.dc = self.out.view
+
+    def entry(self):
+        return (self.kind, self.dA, self.dx, self.dc, self.alpha, self.m, self.n, self.ld)
+
+    def check(self):
+        if self.kind == gb.BATCH_GER_F32:
+            got = self.dA.cpu().numpy()
+            want = oracle.ger(0, self.m, self.n, self.alpha, self.vec_m, self.vec_n, self.A, self.ld)
+            live = ~np.isnan(self.A)
+            assert np.array_equal(got[live].view(np.uint32), want[live].view(np.uint32)), (self.m, self.n)
+            assert np.all(np.isnan(got[~live])), "GER wrote padding"
+            return
+        got = self.out.result()
+        if self.alpha == 0 or self.m == 0 or self.n == 0:
+            assert np.array_equal(got.view(np.uint32), self.vec_m.view(np.uint32))
+            return
+        want = oracle.gemv(0, self.m, self.n, self.alpha, self.A, self.ld, self.vec_n, self.vec_m)
+        scale = oracle.gemv_scale(0, self.m, self.n, self.alpha, self.A, self.ld, self.vec_n, self.vec_m)
+        assert rel_err(got, want, scale) <= TOL, (self.kind, self.m, self.n, self.ld)
+
+
+MIXED_SHAPES = ((1, 1, 0, 0), (3, 5, 1, 0), (300, 257, 0, 0), (97, 1027, 5, 0), (40, 4096, 0, 0),
+                (1000, 33, 0, 0), (17, 999, 1, 1), (2, 20000, 0, 0), (4097, 64, 0, 0), (374, 59, 5, 0),
+                (70, 61, 3, 0), (9, 4098, 6, 0), (300, 3, 5, 0), (5, 2, 6, 0), (33, 1, 7, 0), (50, 16, 0, 3))
+
+
+@pytest.mark.parametrize("lpr", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("u", [1, 2, 4])
+def test_mixed_kinds_every_variant(lpr, u):
+    """FP32 GEMV, BF16 GEMV and GER items in one launch, 16-byte and scalar
+    paths (pads make lda * element bytes a multiple of 16 or not)."""
+    table = gb.tuning_table({b: (lpr, u, 4096 if b % 2 else 65536) for b in range(gb.BATCH_BUCKETS)})
+    items = []
+    for k, (m, n, pad, mis) in enumerate(MIXED_SHAPES):
+        for kind in (gb.BATCH_GEMV_F32, gb.BATCH_GEMV_BF16, gb.BATCH_GER_F32):
+            items.append(Item(kind, m, n, pad, (0.5, -1.25, 0.0)[k % 3] if k % 5 else 0.75,
+                              1000 * lpr + 100 * u + 10 * k + kind, mis))
+    b = gb.Batch.from_items([it.entry() for it in items], table=table)
+    b.launch()
+    torch.cuda.synchronize()
+    for it in items:
+        it.check()

@@ -1,0 +1,129 @@
+"""The serving engine on the GPU: a Poisson stream of GEMV (FP32 and
+BF16-stored A), DOT and GER requests served with continuous batching, every
+result against the CPU oracle on the same inputs (the engine draws operands
+from the documented counter-based generator; synth reproduces them here):
+
+* GEMV FP32, DOT: condition-aware relative error <= 1e-5 (FP32 tolerance);
+* GEMV BF16: <= 1e-5 against the oracle on the decoded BF16 matrix (the
+  same FP32 accumulation as the FP32 form);
+* GER: bit-exact (one fma per element).
+
+Also: a request's result is bit-identical alone and in the mix, a small
+HBM budget is respected while every request completes, and a result buffer
+that is not page-locked is refused."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2108_02025_gb300 as gb
+import synth
+from gpu_util import rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def round_up(v, a):
+    return (v + a - 1) // a * a
+
+
+def operands(op, form, m, n, seed):
+    if op == gb.REQ_GEMV:
+        ld = round_up(n, 8 if form == gb.FORM_BF16 else 4)
+        A = synth.uniform(m * ld, seed, 1, np.float32).reshape(m, ld)[:, :n]
+        if form == gb.FORM_BF16:
+            A = oracle.bf16_decode(oracle.bf16_encode(A.ravel())).reshape(m, n)
+        return np.ascontiguousarray(A), synth.uniform(n, seed, 2, np.float32), synth.uniform(m, seed, 3, np.float32)
+    if op == gb.REQ_DOT:
+        return synth.uniform(n, seed, 1, np.float32), synth.uniform(n, seed, 2, np.float32), \
+            synth.uniform(1, seed, 3, np.float32)
+    ld = round_up(n, 4)
+    C = np.ascontiguousarray(synth.uniform(m * ld, seed, 1, np.float32).reshape(m, ld)[:, :n])
+    return C, synth.uniform(m, seed, 2, np.float32), synth.uniform(n, seed, 3, np.float32)
+
+
+def out_elems(op, m, n):
+    return m if op == gb.REQ_GEMV else 1 if op == gb.REQ_DOT else m * n
+
+
+def check(req, got):
+    op, form, m, n, alpha, seed = req
+    if op == gb.REQ_GEMV:
+        A, x, c0 = operands(op, form, m, n, seed)
+        want = oracle.gemv(0, m, n, alpha, A.ravel(), n, x, c0)
+        scale = oracle.gemv_scale(0, m, n, alpha, A.ravel(), n, x, c0)
+        assert rel_err(got, want, scale) <= 1e-5, req
+    elif op == gb.REQ_DOT:
+        x, y, a0 = operands(op, form, m, n, seed)
+        want = oracle.dot(n, x, y, float(a0[0]))
+        scale = oracle.dot_scale(n, x, y, float(a0[0]))
+        assert abs(float(got[0]) - want) <= 1e-5 * scale, req
+    else:
+        C, x, y = operands(op, form, m, n, seed)
+        want = oracle.ger(0, m, n, alpha, x, y, C.ravel(), n)
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), req
+
+
+def stream(count, seed, lo=1, hi=1500, rate=20000.0, bf16_share=0.5):
+    u = (synth.uniform(count, seed, 31) + 1.0) / 2.0
+    t = np.cumsum(-np.log1p(-u) / rate * 1e9).astype(np.int64)
+    pick = (synth.uniform(count, seed, 32) + 1.0) / 2.0
+    ops = np.where(pick < 0.7, gb.REQ_GEMV, np.where(pick < 0.9, gb.REQ_DOT, gb.REQ_GER))
+    form = np.where((synth.uniform(count, seed, 33) + 1.0) / 2.0 < bf16_share, gb.FORM_BF16, gb.FORM_F32)
+    m = synth.log_uniform_integers(count, seed, 34, lo, hi)
+    n = synth.log_uniform_integers(count, seed, 35, lo, hi)
+    reqs = []
+    for i in range(count):
+        op = int(ops[i])
+        reqs.append((op, int(form[i]) if op == gb.REQ_GEMV else gb.FORM_F32, int(m[i]), int(n[i]),
+                     0.75 if i % 2 else -1.25, seed * 100000 + i))
+    return reqs, t
+
+
+def serve(reqs, offsets, budget=4 << 30, streams=4, max_step=256, start_delay_ns=50_000_000):
+    outs = []
+    with gb.Engine(budget, streams=streams, max_inflight=4096, max_step_requests=max_step) as e:
+        t0 = e.now_ns() + start_delay_ns
+        for i, (op, form, m, n, alpha, seed) in enumerate(reqs):
+            out = torch.empty(out_elems(op, m, n), dtype=torch.float32, pin_memory=True)
+            outs.append(out)
+            assert e.submit(i, op, m, n, alpha, seed, out, arrival_ns=int(t0 + offsets[i]),
+                            form=form) == gb.GB_OK
+        assert e.drain(120000) == gb.GB_OK
+        done = e.poll()
+        stats = e.stats()
+    assert len(done) == len(reqs) and all(c["status"] == gb.GB_OK for c in done)
+    return [o.numpy().copy() for o in outs], done, stats
+
+
+def test_poisson_mix_against_oracle():
+    reqs, t = stream(120, 0)
+    outs, done, stats = serve(reqs, t)
+    assert stats["steps"] >= 2 and stats["completed"] == len(reqs)
+    for r, o in zip(reqs, outs):
+        check(r, o)
+
+
+def test_alone_equals_mix_bit_exact():
+    reqs, t = stream(60, 1, rate=200000.0)
+    mixed, done, stats = serve(reqs, t)
+    assert max(np.bincount([c["step"] for c in done])) > 1, "the mix shares steps"
+    for i in (0, 3, 7, 12, 25, 40, 59):
+        alone, _, _ = serve([reqs[i]], [0], streams=1)
+        assert np.array_equal(alone[0].view(np.uint32), mixed[i].view(np.uint32)), reqs[i]
+
+
+def test_small_budget_every_request_completes_within_it():
+    reqs, t = stream(80, 2, lo=200, hi=1500, rate=1e6)
+    budget = 32 << 20
+    outs, done, stats = serve(reqs, t, budget=budget)
+    assert stats["bytes_peak"] <= budget
+    for r, o in list(zip(reqs, outs))[::8]:
+        check(r, o)
+
+
+def test_pageable_result_buffer_is_refused():
+    with gb.Engine(1 << 30) as e:
+        out = np.zeros(16, np.float32)
+        assert e.submit(0, gb.REQ_GEMV, 16, 16, 1.0, 0, out.ctypes.data) == -2
+        assert e.stats()["submitted"] == 0
