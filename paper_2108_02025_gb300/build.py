@@ -78,5 +78,31 @@ def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False) 
     return LIB
 
 
+def build_variant(out_dir: str, defines: dict, recompile=("api.cu",)) -> str:
+    """A copy of the library with compile-time constants overridden
+    (``-D name=value``) in the files named by ``recompile``; the other
+    objects are those of the main build.  Used by tuning studies."""
+    build()
+    os.makedirs(out_dir, exist_ok=True)
+    cc = nvcc()
+    flags = [f"-D{k}={v}" for k, v in sorted(defines.items())]
+    objs = []
+    for src in _sources():
+        name = os.path.basename(src)
+        if name in recompile:
+            obj = os.path.join(out_dir, name + ".o")
+            r = subprocess.run([cc, *ARCH, *FLAGS, *flags, "-c", src, "-o", obj], capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+        else:
+            obj = os.path.join(BUILD, name + ".o")
+        objs.append(obj)
+    lib = os.path.join(out_dir, "libgbblas.so")
+    r = subprocess.run([cc, *ARCH, "-shared", "-o", lib, *objs], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    return lib
+
+
 if __name__ == "__main__":
     print(build(verbose=True, ptxas_info="-v" in sys.argv, force=True))

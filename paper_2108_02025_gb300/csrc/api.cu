@@ -16,7 +16,13 @@ namespace {
 // 2 blocks x 8 warps (shared memory allows two blocks per SM).
 constexpr int64_t kWaveWarps = 2432;
 constexpr int kMaxSplits = 4096;
-constexpr int64_t kDotSmall = 16384;    // up to here DOT is one block (Alg. 3)
+// DOT is one block (Alg. 3) while one vector holds at most this many bytes,
+// else blocks of the index range (Alg. 4); the crossover measured on GB300
+// (dot_cutoff.py).  A compile-time constant so that studies can rebuild it.
+#ifndef GB_DOT_SMALL_BYTES
+#define GB_DOT_SMALL_BYTES 65536
+#endif
+constexpr int64_t kDotSmallBytes = GB_DOT_SMALL_BYTES;
 constexpr int64_t kDotBlocks = 608;     // large DOT: at most this many blocks (Alg. 4)
 constexpr int kDotPack = 4;             // packs per thread per step in the DOT kernel
 
@@ -224,7 +230,7 @@ inline ColShape col_shape(size_t e, bool vec, int64_t m, int64_t n) {
 }
 
 inline void dot_shape(size_t e, bool vec, int64_t n, int64_t* chunk, int64_t* blocks) {
-  if (n <= kDotSmall) {
+  if (n <= kDotSmallBytes / (int64_t)e) {
     *chunk = n;
     *blocks = 1;
     return;

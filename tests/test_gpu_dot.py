@@ -58,11 +58,27 @@ def test_misaligned(dt, misalign):
         check(dt, n, seed=3, misalign=misalign)
 
 
+def single_block_limit(dt):
+    """Largest n that DOT runs as one block: the workspace (partials of the
+    blocks) is empty exactly there."""
+    code = gb.F64 if dt == np.float64 else gb.F32
+    lo, hi = 1, 1 << 30
+    while lo < hi:
+        mid = (lo + hi + 1) // 2
+        if gb.gb_workspace_bytes(gb.OP_DOT, code, 0, 0, mid) == 0:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
 @pytest.mark.parametrize("dt", DTYPES, ids=DT_IDS)
 def test_small_and_large_regimes_agree(dt):
     """At the single-block / multi-block boundary both forms match the
     oracle (the paper's small/large cutoff, Sec. 4.3.1)."""
-    for n in (16384, 16385):
+    b = single_block_limit(dt)
+    assert 1024 <= b < 1 << 24
+    for n in (b - 1, b, b + 1, b + 7):
         check(dt, n, seed=5)
 
 
