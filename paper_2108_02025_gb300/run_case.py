@@ -4,10 +4,12 @@
     python -m paper_2108_02025_gb300.run_case dot f64 - 1 268435456
     python -m paper_2108_02025_gb300.run_case ger f64 col 16384 16384
     python -m paper_2108_02025_gb300.run_case gemvq e4m3 row 32768 32768
+    python -m paper_2108_02025_gb300.run_case batch f32 row 256 0
 
 Inputs are uniform[-1,1] from the synth generator (seed 0), written on the
 device; for ``gemvq`` (A stored as BF16 or E4M3 with per-row scales) A is
-N(0,1) with rows scaled by 10^U[-3,3], quantised before timing.  Each call is timed with CUDA events on the launching stream; the
+N(0,1) with rows scaled by 10^U[-3,3], quantised before timing; for ``batch`` (one batched launch of m FP32 GEMVs,
+sizes log-uniform in [32, 8192], the autotuned table) n is ignored.  Each call is timed with CUDA events on the launching stream; the
 median is reported with the algorithmic bytes (every element touched once)
 per second.  Used to profile one kernel in isolation.
 """
@@ -26,7 +28,7 @@ if ROOT not in sys.path:
 
 def main(argv=None):
     p = argparse.ArgumentParser(description="one GEMV / DOT / GER case")
-    p.add_argument("op", choices=["gemv", "dot", "ger", "gemvq"])
+    p.add_argument("op", choices=["gemv", "dot", "ger", "gemvq", "batch"])
     p.add_argument("dtype", choices=["f32", "f64", "bf16", "e4m3"])
     p.add_argument("layout", choices=["row", "col", "-"])
     p.add_argument("m", type=int)
@@ -61,6 +63,12 @@ def main(argv=None):
         del A
         call = lambda: gb.gemv_q(Q, sc, x, c, 1.0, n=n)
         nbytes = (2 if args.dtype == "bf16" else 1) * m * n + 4 * n + 8 * m + (4 * m if sc is not None else 0)
+    elif args.op == "batch":
+        import bench
+        wl = bench.BatchWorkload(torch.device("cuda", torch.cuda.current_device()), count=m)
+        b = gb.Batch(wl.problems, table=gb.load_tuning())
+        call = lambda: b.launch()
+        nbytes = wl.bytes
     elif args.op == "dot":
         x, y, a = filled(n, 4), filled(n, 5), filled(1, 6)
         call = lambda: gb.dot(x, y, a, n)
