@@ -170,6 +170,7 @@ struct RowShape {
   GemvPlan::Kind kind;
   int lpr;
   bool long_chain;
+  bool multi;  // FP64 long rows in groups of kRowMultiR
   SplitShape sp;
 };
 
@@ -183,10 +184,20 @@ inline RowShape row_shape(size_t e, bool vec, int64_t m, int64_t n) {
     r.sp = SplitShape{1, 1, 1, n, cdiv(m, 256 / r.lpr)};
     return r;
   }
+  if (vec && e == 8 && m >= kRowMultiMinRows) {  // FP64 long rows: (row group, chunk) units
+    r.kind = GemvPlan::kRowLong;
+    r.multi = true;
+    const int64_t quantum = 256 * V;
+    SplitShape s = block_split(cdiv(m, kRowMultiR), n, quantum * kRowMultiU, quantum, e, 152 * kRowMultiB);
+    s.G = s.S;  // one counter per row group, the group's S partials summed in one level
+    s.NG = 1;
+    r.sp = s;
+    return r;
+  }
   if (vec) {  // long rows: blocks stream (row, chunk) units; one counter per row
     r.kind = GemvPlan::kRowLong;
     const int64_t quantum = 256 * V;
-    SplitShape s = block_split(m, n, quantum * kRowLongU * (e == 8 ? 2 : 1), quantum, e);
+    SplitShape s = block_split(m, n, quantum * (e == 8 ? kRowLongU64 : kRowLongU), quantum, e);
     s.G = s.S;   // the long-row kernel sums a row's S partials in one level
     s.NG = 1;
     r.sp = s;
@@ -353,6 +364,7 @@ int gemv(int layout, int64_t m, int64_t n, T alpha, const T* A, int64_t lda, con
     p.lpr = r.lpr;
     p.long_chain = r.long_chain;
     s = r.sp;
+    p.multi = r.multi;
   } else {
     const ColShape cs = col_shape(e, vec, m, n);
     p.kind = GemvPlan::kCol;

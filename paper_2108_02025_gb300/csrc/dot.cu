@@ -25,12 +25,17 @@ struct DotAcc;
 
 template <>
 struct DotAcc<double> {
-  double a0 = 0.0, a1 = 0.0;
+  // four independent chains: the FP64 fma's latency is long on GB300
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
   __device__ __forceinline__ void add(double x, double y, int k) {
-    if (k & 1) a1 = __fma_rn(x, y, a1);
-    else a0 = __fma_rn(x, y, a0);
+    switch (k & 3) {
+      case 0: a0 = __fma_rn(x, y, a0); break;
+      case 1: a1 = __fma_rn(x, y, a1); break;
+      case 2: a2 = __fma_rn(x, y, a2); break;
+      default: a3 = __fma_rn(x, y, a3); break;
+    }
   }
-  __device__ __forceinline__ double total() const { return __dadd_rn(a0, a1); }
+  __device__ __forceinline__ double total() const { return __dadd_rn(__dadd_rn(a0, a1), __dadd_rn(a2, a3)); }
 };
 
 // Two independent Dot2 chains (p: running sum, s: running error).

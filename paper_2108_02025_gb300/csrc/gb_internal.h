@@ -23,7 +23,19 @@ struct GemvArgs {
 };
 
 // Tuning constants shared by the planner (api.cu) and the kernels.
-constexpr int kRowLongU = 4;     // packs in flight per thread, long-row kernel
+constexpr int kRowLongU = 4;     // packs in flight per thread, long-row kernel (FP32)
+constexpr int kRowLongU64 = 8;   // the same for FP64
+constexpr int kRowLongD64 = 4;   // of those, packs formed on the FP64 pipe (the rest emulated)
+constexpr int kRowLongB64 = 4;   // FP64 long-row kernel: resident blocks per SM budgeted for
+// FP64 long rows without a split: R rows per unit share each load and split
+// of x; U packs per row in flight, D of them on the FP64 pipe; B blocks/SM.
+constexpr int kRowMultiR = 2;
+constexpr int kRowMultiU = 4;
+constexpr int kRowMultiD = 1;
+constexpr int kRowMultiB = 3;
+constexpr int kRowMultiMinRows = 16;  // fewer FP64 rows take the one-row long kernel
+constexpr int kRowShortD64 = 2;  // FP64 short rows: of a lane's 8 packs, those on the FP64 pipe
+constexpr int kRowShortB64 = 4;  // FP64 short rows: resident blocks per SM budgeted for
 constexpr int kRowScalarRW = 4;  // rows per lane group, misaligned row-major kernel
 constexpr int kColTileU = 8;     // columns in flight per thread, column-major tile kernel
 // BF16 / E4M3 GEMV (index: 0 BF16, 1 E4M3): rows sharing each load of x,
@@ -41,6 +53,7 @@ struct GemvPlan {
   Kind kind;
   bool vec;         // 16-byte packs (A, x 16-byte aligned and lda a multiple of the pack)
   bool long_chain;  // FP32 only: a thread sums more than 64 products of one row
+  bool multi;       // FP64 long rows: the kernel with kRowMultiR rows per unit
   int lpr;          // row-major short / scalar: lanes per row (1..32)
   int txw;          // column-major: lanes along the rows of a warp item (1..32)
   int64_t kc;       // columns per chunk

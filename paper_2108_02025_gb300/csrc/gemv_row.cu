@@ -45,7 +45,7 @@ __device__ __forceinline__ T block_total(T v, T* red) {
 
 // Long rows.  unit u = (row u / S, chunk u % S).
 template <typename T, int V, int U, bool LONG>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowLongB64 : 4)
     gemv_row_long_kernel(int64_t m, int64_t n, T alpha, const T* __restrict__ A, int64_t lda,
                          const T* __restrict__ x, T* __restrict__ c, const Split sp, int64_t KC,
                          int64_t units) {
@@ -53,7 +53,8 @@ __global__ void __launch_bounds__(kThreads, 4)
   // LONG (FP32 only): a thread's chain would exceed 64 products, so every
   // FLUSH bodies it is folded into a compensated FP32 sum (TwoSum)
   constexpr int FLUSH = LONG ? (64 / (U * V) > 0 ? 64 / (U * V) : 1) : 1 << 30;
-  constexpr int EFLUSH = 32 / ((U - U / 2) * V) > 0 ? 32 / ((U - U / 2) * V) : 1;
+  constexpr int UD = sizeof(T) == 8 ? (kRowLongD64 < U ? kRowLongD64 : U) : U;  // packs on the FP64 pipe
+  constexpr int EFLUSH = (U - UD) * V > 0 && 32 / ((U - UD) * V) > 0 ? 32 / ((U - UD) * V) : 1;
   __shared__ double red_d[kThreads / 32];
   __shared__ int flag;
   T* red = reinterpret_cast<T*>(red_d);
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(kThreads, 4)
         // mask), so that the emulated path holds no FP64 instruction (a
         // predicated-off one would still occupy the FP64 pipe).
 #pragma unroll
-        for (int q = 0; q < U / 2; ++q)
+        for (int q = 0; q < UD; ++q)
 #pragma unroll
           for (int v = 0; v < V; ++v) {  // two FP64 chains (v), half the dependent latency
             if (v == 0) acc = fma_rn(ap[q].v[v], xp[q].v[v], acc);
@@ -98,12 +99,12 @@ __global__ void __launch_bounds__(kThreads, 4)
           }
         bool ok = true;
 #pragma unroll
-        for (int q = U / 2; q < U; ++q)
+        for (int q = UD; q < U; ++q)
 #pragma unroll
           for (int v = 0; v < V; ++v) ok = ok && emu_ok(ap[q].v[v]) && emu_ok(xp[q].v[v]);
         if (__all_sync(__activemask(), ok)) {
 #pragma unroll
-          for (int q = U / 2; q < U; ++q)
+          for (int q = UD; q < U; ++q)
 #pragma unroll
             for (int v = 0; v < V; ++v) {
               float ah, al, xh, xl;
@@ -112,13 +113,13 @@ __global__ void __launch_bounds__(kThreads, 4)
               emu_fma(ah, al, xh, xl, eh, el);
             }
         } else {
-          DPacks<(U - U / 2) * V> dp;
+          DPacks<(U - UD) * V> dp;
 #pragma unroll
-          for (int q = U / 2; q < U; ++q)
+          for (int q = UD; q < U; ++q)
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-              dp.a[(q - U / 2) * V + v] = ap[q].v[v];
-              dp.x[(q - U / 2) * V + v] = xp[q].v[v];
+              dp.a[(q - UD) * V + v] = ap[q].v[v];
+              dp.x[(q - UD) * V + v] = xp[q].v[v];
             }
           acc = dfma_fallback(dp, acc);
         }
@@ -180,11 +181,183 @@ __global__ void __launch_bounds__(kThreads, 4)
   }
 }
 
+// The last block to finish a chunk of row group `grp` (rows row0 ..
+// row0 + R - 1) sums each row's S chunk partials: thread t adds chunks t,
+// t+256, ... in order, then the fixed block order; out of line, so that the
+// streaming loop keeps its registers.  Every thread of the block calls it.
+__device__ __noinline__ void multi_split_finish(const Split sp, int64_t grp, int64_t row0, int R, int64_t m,
+                                                double alpha, double* __restrict__ c, double* red, int* flag) {
+  const int S = sp.S;
+  if (!arrive_last(sp.tickets + grp, (unsigned)S, flag)) return;
+  for (int r = 0; r < R && row0 + r < m; ++r) {
+    double p = 0.0;
+    for (int q = threadIdx.x; q < S; q += kThreads) p = __dadd_rn(p, __ldcg(sp.part + (int64_t)q * m + row0 + r));
+    p = group_sum<32>(p);
+    __syncthreads();  // red is free
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = p;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) sum = sum + red[w];
+      c[row0 + r] = update_from(c[row0 + r], alpha, sum);
+    }
+  }
+  if (threadIdx.x == 0) sp.tickets[grp] = 0u;
+}
+
+// FP64 long rows: a unit is a group of R consecutive rows times a chunk of
+// KC columns, so each 16-byte load of x, and each cut of an x value into
+// FP32 parts for the emulated products, serves R rows; per row the first D
+// of the U packs in flight go to the FP64 pipe (two chains), the rest to
+// emu_fma, voted per iteration as in the long-row kernel.  A group's missing
+// rows (past m) re-read row m-1 and are dropped.  Block b takes the units
+// [b*units/G, (b+1)*units/G); with S > 1 chunks the block that finishes a
+// group sums each row's S partials in chunk order (one counter per group).
+template <int R, int U, int D>
+__global__ void __launch_bounds__(kThreads, kRowMultiB)
+    gemv_row_multi_f64_kernel(int64_t m, int64_t n, double alpha, const double* __restrict__ A, int64_t lda,
+                              const double* __restrict__ x, double* __restrict__ c, const Split sp,
+                              int64_t KC, int64_t units) {
+  constexpr int V = 2;
+  constexpr int64_t STEP = (int64_t)kThreads * V;
+  constexpr int NE = (U - D) * V;  // emulated products per row per iteration
+  constexpr int EFLUSH = NE > 0 && 32 / NE > 0 ? 32 / NE : 1;
+  static_assert(D < U, "some packs are emulated");
+  __shared__ double red[R][kThreads / 32];
+  __shared__ int flag;
+
+  const int S = sp.S;
+  const int64_t u0 = units * blockIdx.x / gridDim.x;
+  const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
+  const int64_t jlast = (int64_t)(31 - (threadIdx.x & 31)) * V;
+  for (int64_t u = u0; u < u1; ++u) {
+    const int64_t grp = u / S;
+    const int s = (int)(u - grp * S);
+    const int64_t row0 = grp * R;
+    const int64_t k0 = (int64_t)s * KC;
+    const int64_t k1 = (k0 + KC < n) ? k0 + KC : n;
+    const int64_t kv1 = k0 + ((k1 - k0) / V) * V;
+    const double* Ar[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) Ar[r] = A + (row0 + r < m ? row0 + r : m - 1) * lda;
+    double acc[R], acc2[R];
+    float eh[R], el[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      acc[r] = acc2[r] = 0.0;
+      eh[r] = el[r] = 0.f;
+    }
+    int body = 0;
+    int64_t j = k0 + (int64_t)threadIdx.x * V;
+#pragma unroll 1
+    for (; j + jlast + (U - 1) * STEP < kv1; j += U * STEP) {
+      Pack<double, V> xp[U], ap[R][U];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int q = 0; q < U; ++q) ap[r][q] = ld_stream<double, V>(Ar[r] + j + q * STEP);
+#pragma unroll
+      for (int q = 0; q < U; ++q) xp[q] = ld_keep<double, V>(x + j + q * STEP);
+#pragma unroll
+      for (int q = 0; q < D; ++q)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          acc[r] = __fma_rn(ap[r][q].v[0], xp[q].v[0], acc[r]);
+          acc2[r] = __fma_rn(ap[r][q].v[1], xp[q].v[1], acc2[r]);
+        }
+      bool ok = true;
+#pragma unroll
+      for (int q = D; q < U; ++q)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          ok = ok && emu_ok(xp[q].v[v]);
+#pragma unroll
+          for (int r = 0; r < R; ++r) ok = ok && emu_ok(ap[r][q].v[v]);
+        }
+      if (__all_sync(__activemask(), ok)) {
+#pragma unroll
+        for (int q = D; q < U; ++q)
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            float xh, xl;
+            emu_split(xp[q].v[v], xh, xl);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              float ah, al;
+              emu_split(ap[r][q].v[v], ah, al);
+              emu_fma(ah, al, xh, xl, eh[r], el[r]);
+            }
+          }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          DPacks<NE> dp;
+#pragma unroll
+          for (int q = D; q < U; ++q)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              dp.a[(q - D) * V + v] = ap[r][q].v[v];
+              dp.x[(q - D) * V + v] = xp[q].v[v];
+            }
+          acc[r] = dfma_fallback(dp, acc[r]);
+        }
+      }
+      if (++body == EFLUSH) {  // at most 32 products in each FP32 pair
+        body = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          acc[r] = __dadd_rn(acc[r], __dadd_rn((double)eh[r], (double)el[r]));
+          eh[r] = el[r] = 0.f;
+        }
+      }
+    }
+#pragma unroll 1
+    for (; j < kv1; j += STEP) {  // remaining whole packs, one at a time
+      const Pack<double, V> xq = ld_keep<double, V>(x + j);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const Pack<double, V> aq = ld_stream<double, V>(Ar[r] + j);
+        acc[r] = __fma_rn(aq.v[0], xq.v[0], acc[r]);
+        acc2[r] = __fma_rn(aq.v[1], xq.v[1], acc2[r]);
+      }
+    }
+    if (kv1 + threadIdx.x < k1) {  // ragged end (one column)
+      const int64_t jj = kv1 + threadIdx.x;
+      const double xj = __ldg(x + jj);
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = __fma_rn(__ldcs(Ar[r] + jj), xj, acc[r]);
+    }
+
+    // fixed-order block sums (warp butterfly, then warps in order)
+    __syncthreads();  // red is free
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const double v = group_sum<32>(__dadd_rn(__dadd_rn(acc[r], acc2[r]), __dadd_rn((double)eh[r], (double)el[r])));
+      if ((threadIdx.x & 31) == 0) red[r][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    const int64_t row = row0 + threadIdx.x;  // thread r < R finishes row row0 + r
+    const bool mine = threadIdx.x < R && row < m;
+    double t = 0.0;
+    if (mine) {
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) t = t + red[threadIdx.x][w];
+    }
+    if (S == 1) {
+      if (mine) c[row] = update(c[row], alpha, t);
+      continue;
+    }
+    if (mine) sp.part[(int64_t)s * m + row] = t;
+    multi_split_finish(sp, grp, row0, R, m, alpha, c, red[0], &flag);
+  }
+}
+
 // Short rows (S = 1, at most 32*8 packs).  LPR lanes per row, each with up
 // to 8 packs (pack k*LPR + l of the row), so a block iteration reads
 // 256/LPR consecutive rows; block b takes rows [b*m/G, (b+1)*m/G).
 template <typename T, int V, int LPR>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? 3 : 4)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowShortB64 : 4)
     gemv_row_short_kernel(int64_t m, int64_t n, T alpha, const T* __restrict__ A, int64_t lda,
                           const T* __restrict__ x, T* __restrict__ c) {
   constexpr int GROUPS = kThreads / LPR;  // rows per block iteration
@@ -197,6 +370,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? 3 : 4)
   const int64_t kv1 = packs * V;
   const bool tail = kv1 + l < n;  // ragged end: lane l takes column kv1 + l
   const T xt = tail ? __ldg(x + kv1 + l) : T(0);
+  // FP64: x is cut into FP32 parts once per block, into shared memory (NaN
+  // marks a value outside the emulated range); short rows have at most 512
+  // FP64 columns
+  constexpr int PD = sizeof(T) == 8 ? kRowShortD64 : PMAX;  // packs on the FP64 pipe
+  __shared__ float2 xs[sizeof(T) == 8 ? 256 * V : 1];
+  if constexpr (sizeof(T) == 8) {
+    for (int64_t col = threadIdx.x; col < kv1; col += kThreads) {
+      const double d = __ldg(x + col);
+      float h = __int_as_float(0x7FC00000), lo = 0.f;
+      if (emu_ok(d)) emu_split(d, h, lo);
+      xs[col] = make_float2(h, lo);
+    }
+    __syncthreads();
+  }
 
   // every thread runs the same number of iterations (the butterfly needs
   // whole warps); rows past r1 are predicated off
@@ -213,12 +400,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? 3 : 4)
     }
     T acc = (ok && tail) ? __ldcs(Ar + kv1 + l) * xt : T(0);
     if constexpr (sizeof(T) == 8) {
-      // FP64: packs 0..3 on the FP64 pipe, packs 4..7 with FP32 instructions
-      // (emu_fma) when every lane of the warp has all of them in range; the
-      // choice is made for the whole warp, so that the emulated path holds no
-      // FP64 instruction.
+      // FP64: packs 0..PD-1 on the FP64 pipe, packs PD..7 with FP32
+      // instructions (emu_fma, x cut once per block above) when every lane
+      // of the warp has all of them in range; the choice is made for the
+      // whole warp, so that the emulated path holds no FP64 instruction.
 #pragma unroll
-      for (int k = 0; k < PMAX / 2; ++k) {
+      for (int k = 0; k < PD; ++k) {
         const int64_t p = (int64_t)k * LPR + l;
         if (ok && p < packs) {
           const Pack<T, V> xp = ld_keep<T, V>(x + p * V);
@@ -226,42 +413,46 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? 3 : 4)
           for (int v = 0; v < V; ++v) acc = fma_rn(ap[k].v[v], xp.v[v], acc);
         }
       }
-      Pack<T, V> xq[PMAX / 2];
+      // packs past the row or of a row past r1 take no part (they add 0)
       bool good = true;
 #pragma unroll
-      for (int k = PMAX / 2; k < PMAX; ++k) {
+      for (int k = PD; k < PMAX; ++k) {
         const int64_t p = (int64_t)k * LPR + l;
-        const bool present = ok && p < packs;
+        if (ok && p < packs) {
 #pragma unroll
-        for (int v = 0; v < V; ++v) xq[k - PMAX / 2].v[v] = T(0);
-        if (present) xq[k - PMAX / 2] = ld_keep<T, V>(x + p * V);
-        good = good && present;
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-          good = good && emu_ok(ap[k].v[v]) && emu_ok(xq[k - PMAX / 2].v[v]);
+          for (int v = 0; v < V; ++v) good = good && emu_ok(ap[k].v[v]) && !isnan(xs[p * V + v].x);
+        }
       }
       if (__all_sync(__activemask(), good)) {
         float eh = 0.f, el = 0.f;
 #pragma unroll
-        for (int k = PMAX / 2; k < PMAX; ++k)
+        for (int k = PD; k < PMAX; ++k) {
+          const int64_t p = (int64_t)k * LPR + l;
+          if (ok && p < packs) {
 #pragma unroll
-          for (int v = 0; v < V; ++v) {
-            float ah, al, xh, xl;
-            emu_split(ap[k].v[v], ah, al);
-            emu_split(xq[k - PMAX / 2].v[v], xh, xl);
-            emu_fma(ah, al, xh, xl, eh, el);
+            for (int v = 0; v < V; ++v) {
+              float ah, al;
+              emu_split(ap[k].v[v], ah, al);
+              const float2 xv = xs[p * V + v];
+              emu_fma(ah, al, xv.x, xv.y, eh, el);
+            }
           }
+        }
         acc = __dadd_rn(acc, __dadd_rn((double)eh, (double)el));
       } else {
-        DPacks<(PMAX / 2) * V> dp;
+        DPacks<(PMAX - PD) * V> dp;
 #pragma unroll
-        for (int k = PMAX / 2; k < PMAX; ++k) {
+        for (int k = PD; k < PMAX; ++k) {
           const int64_t p = (int64_t)k * LPR + l;
           const bool present = ok && p < packs;
+          Pack<T, V> xq;
+#pragma unroll
+          for (int v = 0; v < V; ++v) xq.v[v] = T(0);
+          if (present) xq = ld_keep<T, V>(x + p * V);
 #pragma unroll
           for (int v = 0; v < V; ++v) {  // absent packs add 0 * 0
-            dp.a[(k - PMAX / 2) * V + v] = present ? (double)ap[k].v[v] : 0.0;
-            dp.x[(k - PMAX / 2) * V + v] = present ? (double)xq[k - PMAX / 2].v[v] : 0.0;
+            dp.a[(k - PD) * V + v] = present ? (double)ap[k].v[v] : 0.0;
+            dp.x[(k - PD) * V + v] = present ? (double)xq.v[v] : 0.0;
           }
         }
         acc = dfma_fallback(dp, acc);
@@ -345,9 +536,17 @@ __global__ void __launch_bounds__(kThreads, 4)
 
 template <typename T, int V, bool LONG>
 int launch_long(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
+  if constexpr (sizeof(T) == 8) {
+    if (p.multi) {
+      auto kern = gemv_row_multi_f64_kernel<kRowMultiR, kRowMultiU, kRowMultiD>;
+      const int grid = grid_size((const void*)kern, p.units);
+      kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c, p.split, p.kc, p.units);
+      return 0;
+    }
+  }
   // FP64 carries the FP32 emulation of half its products: more work per
   // byte, so more packs in flight per thread
-  auto kern = gemv_row_long_kernel<T, V, sizeof(T) == 8 ? 2 * kRowLongU : kRowLongU, LONG>;
+  auto kern = gemv_row_long_kernel<T, V, sizeof(T) == 8 ? kRowLongU64 : kRowLongU, LONG>;
   const int grid = grid_size((const void*)kern, p.units);
   kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c, p.split, p.kc, p.units);
   return 0;
