@@ -137,7 +137,7 @@ constexpr int64_t kWaveBlocks = 608;
 // `wave` is the number of blocks resident at once.  Depends only on the
 // shape.
 inline SplitShape block_split(int64_t items, int64_t n, int64_t min_kc, int64_t quantum, size_t e,
-                              int64_t wave = kWaveBlocks) {
+                              int64_t wave = kWaveBlocks, int64_t min_units = 4) {
   SplitShape s{1, 1, 1, n > 0 ? n : 1, items};
   int64_t smax = kMaxSplits;
   if (smax > n / min_kc) smax = n / min_kc;
@@ -147,12 +147,12 @@ inline SplitShape block_split(int64_t items, int64_t n, int64_t min_kc, int64_t 
     const double busiest = (double)cdiv(items * S, wave);
     return (u / busiest) * (u < 1.0 ? u : 1.0);
   };
-  if (items >= 4 * wave || smax < 2) return s;
+  if (items >= min_units * wave || smax < 2) return s;
   int64_t best = 1;
   double best_even = even(1);
   for (int64_t S = 2; S <= smax; ++S) {
     const double ev = even(S);
-    if (items * S >= 4 * wave && ev >= 0.95) { best = S; break; }
+    if (items * S >= min_units * wave && ev >= 0.95) { best = S; break; }
     if (ev > best_even + 1e-9) { best = S; best_even = ev; }
   }
   if (best < 2) return s;
@@ -188,7 +188,8 @@ inline RowShape row_shape(size_t e, bool vec, int64_t m, int64_t n) {
     r.kind = GemvPlan::kRowLong;
     r.multi = true;
     const int64_t quantum = 256 * V;
-    SplitShape s = block_split(cdiv(m, kRowMultiR), n, quantum * kRowMultiU, quantum, e, 152 * kRowMultiB);
+    SplitShape s = block_split(cdiv(m, kRowMultiR), n, quantum * kRowMultiU, quantum, e, 152 * kRowMultiB,
+                               kRowMinUnits);
     s.G = s.S;  // one counter per row group, the group's S partials summed in one level
     s.NG = 1;
     r.sp = s;
@@ -197,7 +198,8 @@ inline RowShape row_shape(size_t e, bool vec, int64_t m, int64_t n) {
   if (vec) {  // long rows: blocks stream (row, chunk) units; one counter per row
     r.kind = GemvPlan::kRowLong;
     const int64_t quantum = 256 * V;
-    SplitShape s = block_split(m, n, quantum * (e == 8 ? kRowLongU64 : kRowLongU), quantum, e);
+    SplitShape s = block_split(m, n, quantum * (e == 8 ? kRowLongU64 : kRowLongU), quantum, e, kWaveBlocks,
+                               kRowMinUnits);
     s.G = s.S;   // the long-row kernel sums a row's S partials in one level
     s.NG = 1;
     r.sp = s;
@@ -224,10 +226,12 @@ inline ColShape col_shape(size_t e, bool vec, int64_t m, int64_t n) {
   const int64_t V = vec ? 16 / (int64_t)e : 1;
   ColShape c;
   if (vec) {  // block tiles of tx*V rows; tx threads along the rows, 256/tx along the columns
-    const int64_t tx = pow2_at_least(cdiv(m, V), 64);
+    // short columns (n small): up to all 256 threads along the rows, no
+    // cross-lane sum; otherwise at most 64
+    const int64_t tx = pow2_at_least(cdiv(m, V), n <= kColShortN ? 256 : 64);
     const int64_t ty = 256 / tx;
     c.txw = (int)tx;
-    c.sp = block_split(cdiv(m, tx * V), n, ty * kColTileU, 1, e);
+    c.sp = block_split(cdiv(m, tx * V), n, ty * kColTileU, 1, e, kWaveBlocks, kColMinUnits);
     c.long_chain = e == 4 && cdiv(c.sp.kc, ty) > 64;
     return c;
   }

@@ -38,6 +38,9 @@ constexpr int kRowShortD64 = 2;  // FP64 short rows: of a lane's 8 packs, those 
 constexpr int kRowShortB64 = 4;  // FP64 short rows: resident blocks per SM budgeted for
 constexpr int kRowScalarRW = 4;  // rows per lane group, misaligned row-major kernel
 constexpr int kColTileU = 8;     // columns in flight per thread, column-major tile kernel
+constexpr int64_t kColShortN = 512;  // column-major: n up to this takes tiles of up to 256 row threads
+constexpr int64_t kColMinUnits = 1;  // column-major: split until at least this many units per block
+constexpr int64_t kRowMinUnits = 2;  // row-major long rows: the same
 // BF16 / E4M3 GEMV (index: 0 BF16, 1 E4M3): rows sharing each load of x,
 // 16-byte packs per row in flight per thread, and resident blocks per SM
 // the registers are budgeted for.

@@ -345,6 +345,8 @@ template <typename T, int V, bool LONG>
 int by_txw(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
   if constexpr (V > 1) {  // 16-byte aligned operands: block tiles (tx = threads along the rows)
     switch (p.txw) {
+      case 256: return launch_tile<T, V, 256, LONG>(a, p, st);
+      case 128: return launch_tile<T, V, 128, LONG>(a, p, st);
       case 64: return launch_tile<T, V, 64, LONG>(a, p, st);
       case 32: return launch_tile<T, V, 32, LONG>(a, p, st);
       case 16: return launch_tile<T, V, 16, LONG>(a, p, st);
