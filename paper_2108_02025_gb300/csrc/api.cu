@@ -180,7 +180,7 @@ inline RowShape row_shape(size_t e, bool vec, int64_t m, int64_t n) {
   const int64_t packs = cdiv(n, V);
   if (vec && packs <= 256) {  // short rows: lane groups of up to 8 packs each, no split
     r.kind = GemvPlan::kRowShort;
-    r.lpr = (int)pow2_at_least(cdiv(packs, 8), 32);
+    r.lpr = (int)pow2_at_least(cdiv(packs, kRowShortPPL), 32);
     r.sp = SplitShape{1, 1, 1, n, cdiv(m, 256 / r.lpr)};
     return r;
   }

@@ -36,6 +36,7 @@ constexpr int kRowMultiB = 3;
 constexpr int kRowMultiMinRows = 16;  // fewer FP64 rows take the one-row long kernel
 constexpr int kRowShortD64 = 2;  // FP64 short rows: of a lane's 8 packs, those on the FP64 pipe
 constexpr int kRowShortB64 = 4;  // FP64 short rows: resident blocks per SM budgeted for
+constexpr int64_t kRowShortPPL = 8;  // short rows: packs per lane the lanes per row are sized for (<= 8)
 constexpr int kRowScalarRW = 4;  // rows per lane group, misaligned row-major kernel
 constexpr int kColTileU = 8;     // columns in flight per thread, column-major tile kernel
 constexpr int64_t kColShortN = 512;  // column-major: n up to this takes tiles of up to 256 row threads
