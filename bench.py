@@ -626,7 +626,7 @@ def serve_once(count, rate, form, seed=0, sample=8):
     import paper_2108_02025_gb300 as gb
     t, ops, m, n = serve_stream(count, rate, seed)
     gemv_idx = [i for i in range(count) if ops[i] == 0 and m[i] * n[i] <= 1 << 22]
-    picks = set(gemv_idx[::max(1, len(gemv_idx) // sample)][:sample])
+    picks = set(gemv_idx[::max(1, len(gemv_idx) // sample)][:sample]) if sample > 0 else set()
     outs = {}
     with gb.Engine(SERVE_BUDGET, streams=4, max_inflight=16384, max_step_requests=512,
                    table=gb.load_tuning()) as e:
@@ -658,9 +658,9 @@ def serve_once(count, rate, form, seed=0, sample=8):
         mi, ni = int(m[i]), int(n[i])
         ld = (ni + 7) // 8 * 8 if form == gb.FORM_BF16 else (ni + 3) // 4 * 4
         s0 = seed * 1000003 + i
-        A = synth.uniform(mi * ld, s0, 1, np.float32).reshape(mi, ld)[:, :ni].astype(np.float64)
-        x = synth.uniform(ni, s0, 2, np.float32).astype(np.float64)
-        c0 = synth.uniform(mi, s0, 3, np.float32).astype(np.float64)
+        A = synth.uniform_pairs(mi * ld, s0, 1).reshape(mi, ld)[:, :ni].astype(np.float64)
+        x = synth.uniform_pairs(ni, s0, 2).astype(np.float64)
+        c0 = synth.uniform_pairs(mi, s0, 3).astype(np.float64)
         want = c0 + A @ x
         scale = np.abs(c0) + np.abs(A) @ np.abs(x)
         err = max(err, float(np.max(np.abs(out.numpy().astype(np.float64) - want) / scale)))

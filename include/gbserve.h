@@ -32,8 +32,10 @@
  * Operands.  A request's inputs are drawn on the device from the counter-
  * based SplitMix64 generator (Steele, Lea and Flood, OOPSLA 2014) with the
  * request's seed: key(seed, s) = mix(mix(seed + G) ^ (s * 0xD1B54A32D192ED03)),
- * u_k = mix(key + (k + 1) G), value (u_k >> 40) * 2^-23 - 1 (FP32 uniform in
- * [-1, 1)), rounded to nearest even for BF16 storage.  Streams s: GEMV A=1,
+ * one word u_k = mix(key + (k + 1) G) per pair of elements: element 2k takes
+ * b = bits 63..40 of u_k, element 2k+1 bits 39..16, value b * 2^-23 - 1
+ * (FP32 uniform in [-1, 1)), rounded to nearest even for BF16 storage
+ * (synth.uniform_pairs on the host).  Streams s: GEMV A=1,
  * x=2, c=3; DOT x=1, y=2, alpha=3; GER C=1, x=2, y=3.  Matrices are stored
  * row-major with the leading dimension rounded up to 4 elements (FP32) or 8
  * (BF16); element (i, j) takes index k = i * ld + j of its stream.

@@ -55,9 +55,31 @@ struct FillSeg {  // 32 bytes
 };
 static_assert(sizeof(FillSeg) == 32, "fill segment layout");
 
-constexpr int64_t kFillChunk = 16384;  // elements per block
+constexpr int64_t kFillChunk = 16384;  // elements per block (a multiple of 4)
 
-// Block b fills chunk b - first[s] of segment s, the last s with first[s] <= b.
+// Elements 2k and 2k+1 of a stream come from one word u = mix(key + (k+1) G):
+// bits 63..40 and bits 39..16, each b mapped to b * 2^-23 - 1.  The map is
+// done on the bit pattern: 1 + m * 2^-23 (m = the low 23 bits of b) is a
+// binary32 in [1, 2), and subtracting 1 (b >= 2^23) or 2 (b < 2^23) is exact.
+__device__ __forceinline__ float uniform_of(unsigned b24) {
+  const float one_m = __uint_as_float(0x3F800000u | (b24 & 0x7FFFFFu));
+  return __fsub_rn(one_m, (b24 & 0x800000u) ? 1.0f : 2.0f);
+}
+
+__device__ __forceinline__ void pair_of(uint64_t key, int64_t k, float& v0, float& v1) {
+  const uint64_t u = sm_mix(key + (uint64_t)(k + 1) * kG);
+  v0 = uniform_of((unsigned)(u >> 40));
+  v1 = uniform_of((unsigned)(u >> 16) & 0xFFFFFFu);
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  return *reinterpret_cast<const uint16_t*>(&h);
+}
+
+// Block b fills chunk b - first[s] of segment s, the last s with first[s] <= b:
+// four consecutive elements (two words) per thread and step, 16-byte (FP32)
+// or 8-byte (BF16) stores; segments start 256-byte aligned.
 __global__ void __launch_bounds__(kThreads) fill_kernel(const FillSeg* __restrict__ segs,
                                                         const int64_t* __restrict__ first, int nseg) {
   const int64_t b = blockIdx.x;
@@ -70,14 +92,26 @@ __global__ void __launch_bounds__(kThreads) fill_kernel(const FillSeg* __restric
   const FillSeg sg = segs[lo];
   const int64_t e0 = (b - first[lo]) * kFillChunk;
   const int64_t e1 = e0 + kFillChunk < sg.count ? e0 + kFillChunk : sg.count;
-  for (int64_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
-    const uint64_t u = sm_mix(sg.key + (uint64_t)(e + 1) * kG);
-    const float v = __fsub_rn(__fmul_rn((float)(uint32_t)(u >> 40), 0x1p-23f), 1.0f);
+  for (int64_t e = e0 + 4 * (int64_t)threadIdx.x; e < e1; e += 4 * kThreads) {
+    float v[4];
+    pair_of(sg.key, e >> 1, v[0], v[1]);
+    pair_of(sg.key, (e >> 1) + 1, v[2], v[3]);
     if (sg.kind == kFillF32) {
-      static_cast<float*>(sg.dst)[e] = v;
+      float* d = static_cast<float*>(sg.dst) + e;
+      if (e + 4 <= e1) {
+        *reinterpret_cast<float4*>(d) = make_float4(v[0], v[1], v[2], v[3]);
+      } else {
+        for (int q = 0; q < 4 && e + q < e1; ++q) d[q] = v[q];
+      }
     } else {
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
-      static_cast<uint16_t*>(sg.dst)[e] = *reinterpret_cast<const uint16_t*>(&h);
+      uint16_t* d = static_cast<uint16_t*>(sg.dst) + e;
+      if (e + 4 <= e1) {
+        const unsigned lo2 = bf16_bits(v[0]) | ((unsigned)bf16_bits(v[1]) << 16);
+        const unsigned hi2 = bf16_bits(v[2]) | ((unsigned)bf16_bits(v[3]) << 16);
+        *reinterpret_cast<uint2*>(d) = make_uint2(lo2, hi2);
+      } else {
+        for (int q = 0; q < 4 && e + q < e1; ++q) d[q] = bf16_bits(v[q]);
+      }
     }
   }
 }

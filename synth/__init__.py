@@ -92,6 +92,19 @@ def integers(n: int, seed: int, stream: int, lo: int, hi: int, dtype=np.float64,
 _lib = None
 
 
+def uniform_pairs(n: int, seed: int, stream: int, offset: int = 0) -> np.ndarray:
+    """FP32 uniform in [-1, 1) with two elements per word (the serving
+    engine's operands): element 2k takes bits 63..40 of u_k, element 2k+1
+    bits 39..16, each b mapped to b * 2^-23 - 1 (exact)."""
+    if n == 0:
+        return np.zeros(0, np.float32)
+    k = np.arange(offset, offset + n, dtype=np.int64)
+    w0 = offset // 2
+    u = raw((offset + n - 1) // 2 - w0 + 1, seed, stream, w0)[k // 2 - w0]
+    b = np.where(k % 2 == 0, u >> np.uint64(40), (u >> np.uint64(16)) & np.uint64(0xFFFFFF))
+    return (b.astype(np.float32) * np.float32(2.0 ** -23) - np.float32(1.0)).astype(np.float32)
+
+
 def log_uniform_integers(n: int, seed: int, stream: int, lo: int, hi: int) -> np.ndarray:
     """round(exp(ln lo + u (ln hi - ln lo))) with u uniform in [0, 1): sizes
     spread evenly over the decades between lo and hi (int64)."""

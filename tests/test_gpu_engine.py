@@ -1,7 +1,8 @@
 """The serving engine on the GPU: a Poisson stream of GEMV (FP32 and
 BF16-stored A), DOT and GER requests served with continuous batching, every
 result against the CPU oracle on the same inputs (the engine draws operands
-from the documented counter-based generator; synth reproduces them here):
+from the documented counter-based generator; synth.uniform_pairs reproduces
+them here):
 
 * GEMV FP32, DOT: condition-aware relative error <= 1e-5 (FP32 tolerance);
 * GEMV BF16: <= 1e-5 against the oracle on the decoded BF16 matrix (the
@@ -28,18 +29,18 @@ def round_up(v, a):
 
 
 def operands(op, form, m, n, seed):
+    U = synth.uniform_pairs
     if op == gb.REQ_GEMV:
         ld = round_up(n, 8 if form == gb.FORM_BF16 else 4)
-        A = synth.uniform(m * ld, seed, 1, np.float32).reshape(m, ld)[:, :n]
+        A = U(m * ld, seed, 1).reshape(m, ld)[:, :n]
         if form == gb.FORM_BF16:
             A = oracle.bf16_decode(oracle.bf16_encode(A.ravel())).reshape(m, n)
-        return np.ascontiguousarray(A), synth.uniform(n, seed, 2, np.float32), synth.uniform(m, seed, 3, np.float32)
+        return np.ascontiguousarray(A), U(n, seed, 2), U(m, seed, 3)
     if op == gb.REQ_DOT:
-        return synth.uniform(n, seed, 1, np.float32), synth.uniform(n, seed, 2, np.float32), \
-            synth.uniform(1, seed, 3, np.float32)
+        return U(n, seed, 1), U(n, seed, 2), U(1, seed, 3)
     ld = round_up(n, 4)
-    C = np.ascontiguousarray(synth.uniform(m * ld, seed, 1, np.float32).reshape(m, ld)[:, :n])
-    return C, synth.uniform(m, seed, 2, np.float32), synth.uniform(n, seed, 3, np.float32)
+    C = np.ascontiguousarray(U(m * ld, seed, 1).reshape(m, ld)[:, :n])
+    return C, U(m, seed, 2), U(n, seed, 3)
 
 
 def out_elems(op, m, n):
@@ -127,3 +128,15 @@ def test_pageable_result_buffer_is_refused():
         out = np.zeros(16, np.float32)
         assert e.submit(0, gb.REQ_GEMV, 16, 16, 1.0, 0, out.ctypes.data) == -2
         assert e.stats()["submitted"] == 0
+
+
+def test_operands_are_the_documented_generator():
+    """A GER with alpha 0 leaves C as generated: its bits must equal
+    synth.uniform_pairs (stream 1, leading dimension rounded up to 4), for
+    sizes that end on every residue of the four-element store."""
+    reqs = [(gb.REQ_GER, gb.FORM_F32, m, n, 0.0, 77 + k) for k, (m, n) in
+            enumerate(((1, 1), (3, 5), (7, 13), (64, 64), (33, 1023), (5, 4097)))]
+    outs, _, _ = serve(reqs, [0] * len(reqs))
+    for (op, form, m, n, alpha, seed), got in zip(reqs, outs):
+        C, _, _ = operands(op, form, m, n, seed)
+        assert np.array_equal(got.reshape(m, n).view(np.uint32), C.view(np.uint32)), (m, n)

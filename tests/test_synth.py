@@ -58,3 +58,17 @@ def test_cuda_fill_matches_numpy(dtype):
     assert np.array_equal(t.cpu().numpy(), synth.uniform(100003, 9, 4, np.dtype(dtype).type, offset=12345))
     synth.fill_integers(t, 9, 5, -8, 8)
     assert np.array_equal(t.cpu().numpy(), synth.integers(100003, 9, 5, -8, 8, np.dtype(dtype).type))
+
+
+def test_uniform_pairs_definition():
+    """Two FP32 uniforms per word: bits 63..40 then 39..16 of u_k, mapped to
+    b * 2^-23 - 1; any sub-range regenerates on its own."""
+    import numpy as np
+    u = synth.raw(50, 9, 4)
+    b = np.stack([u >> np.uint64(40), (u >> np.uint64(16)) & np.uint64(0xFFFFFF)], 1).ravel()
+    want = b.astype(np.float64) * 2.0 ** -23 - 1.0
+    got = synth.uniform_pairs(100, 9, 4)
+    assert got.dtype == np.float32 and np.array_equal(got.astype(np.float64), want)
+    for off, n in ((1, 10), (7, 33), (0, 1), (99, 1)):
+        assert np.array_equal(synth.uniform_pairs(n, 9, 4, off), got[off:off + n])
+    assert synth.uniform_pairs(0, 9, 4).size == 0
