@@ -8,7 +8,10 @@
 // alpha directly, otherwise the block that finishes last sums the block
 // totals in index order in FP64 and adds them to alpha.
 //
-// FP64 inputs accumulate with FP64 fma.  FP32 inputs use the compensated
+// FP64 inputs: half of each thread's products are FP64 fmas (four chains),
+// the other half are formed with FP32 instructions (exact operand cuts,
+// TwoProduct, TwoSum; gb_common.cuh) when every active lane has them in
+// range, so the small FP64 pipe does not cap the HBM stream.  FP32 inputs use the compensated
 // dot product Dot2 of Ogita, Rump & Oishi ("Accurate sum and dot product",
 // SIAM J. Sci. Comput. 26(6), 2005: TwoProduct by fma, TwoSum by Knuth) in
 // FP32 per thread, so no FP64 operation is spent per element, and move to
@@ -18,6 +21,9 @@
 
 namespace gb {
 namespace {
+
+constexpr int kDotEmu64 = 2;  // FP64: packs per step (of 4) formed on the FP32 pipe
+constexpr int kDotEmuFlush = kDotEmu64 > 0 ? 16 / kDotEmu64 : 1;  // steps per FP32 pair: <= 32 products
 
 // Per-thread accumulator of the sum of products.
 template <typename T>
@@ -73,6 +79,8 @@ __global__ void __launch_bounds__(kThreads, 4)
   constexpr int64_t STEP = (int64_t)kThreads * V;
 
   DotAcc<T> acc;
+  float eh = 0.f, el = 0.f;  // FP64: the pair of the FP32-emulated products
+  int ebody = 0;
   int64_t i = lo + (int64_t)threadIdx.x * V;
   for (; i + (U - 1) * STEP < hv; i += U * STEP) {
     Pack<T, V> xp[U], yp[U];
@@ -81,10 +89,51 @@ __global__ void __launch_bounds__(kThreads, 4)
       xp[q] = ld_stream<T, V>(x + i + q * STEP);
       yp[q] = ld_stream<T, V>(y + i + q * STEP);
     }
+    if constexpr (sizeof(T) == 8 && V == 2 && kDotEmu64 > 0) {
+      // FP64: the last kDotEmu64 packs with FP32 instructions (emu_fma) when
+      // every active lane has them in range, relieving the FP64 pipe
+      constexpr int QE = U - kDotEmu64;
 #pragma unroll
-    for (int q = 0; q < U; ++q)
+      for (int q = 0; q < QE; ++q)
 #pragma unroll
-      for (int v = 0; v < V; ++v) acc.add(xp[q].v[v], yp[q].v[v], q * V + v);
+        for (int v = 0; v < V; ++v) acc.add(xp[q].v[v], yp[q].v[v], q * V + v);
+      bool ok = true;
+#pragma unroll
+      for (int q = QE; q < U; ++q)
+#pragma unroll
+        for (int v = 0; v < V; ++v) ok = ok && emu_ok(xp[q].v[v]) && emu_ok(yp[q].v[v]);
+      if (__all_sync(__activemask(), ok)) {
+#pragma unroll
+        for (int q = QE; q < U; ++q)
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            float xh, xl, yh, yl;
+            emu_split(xp[q].v[v], xh, xl);
+            emu_split(yp[q].v[v], yh, yl);
+            emu_fma(xh, xl, yh, yl, eh, el);
+          }
+        if (++ebody == kDotEmuFlush) {
+          ebody = 0;
+          acc.a3 = __dadd_rn(acc.a3, __dadd_rn((double)eh, (double)el));
+          eh = el = 0.f;
+        }
+      } else {
+        DPacks<kDotEmu64 * V> dp;
+#pragma unroll
+        for (int q = QE; q < U; ++q)
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            dp.a[(q - QE) * V + v] = xp[q].v[v];
+            dp.x[(q - QE) * V + v] = yp[q].v[v];
+          }
+        acc.a2 = dfma_fallback(dp, acc.a2);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < U; ++q)
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc.add(xp[q].v[v], yp[q].v[v], q * V + v);
+    }
   }
   for (; i < hv; i += STEP) {
     const Pack<T, V> xp = ld_stream<T, V>(x + i), yp = ld_stream<T, V>(y + i);
@@ -93,7 +142,7 @@ __global__ void __launch_bounds__(kThreads, 4)
   }
   for (int64_t k = hv + threadIdx.x; k < hi; k += kThreads) acc.add(__ldcs(x + k), __ldcs(y + k), 0);
 
-  const double bsum = block_sum(acc.total(), red);
+  const double bsum = block_sum(__dadd_rn(acc.total(), __dadd_rn((double)eh, (double)el)), red);
 
   if (gridDim.x == 1) {  // one block: Alg. 3, no workspace
     if (threadIdx.x == 0) *alpha = (T)__dadd_rn((double)*alpha, bsum);
