@@ -140,3 +140,35 @@ def test_operands_are_the_documented_generator():
     for (op, form, m, n, alpha, seed), got in zip(reqs, outs):
         C, _, _ = operands(op, form, m, n, seed)
         assert np.array_equal(got.reshape(m, n).view(np.uint32), C.view(np.uint32)), (m, n)
+
+
+def test_full_size_stream_sampled():
+    """The benchmark's serving stream (sizes log-uniform in [32, 16384], 64
+    GB budget, 4 streams, every request arriving at once), 300 requests, with
+    the results of sampled requests of every kind checked against the
+    oracle."""
+    import bench
+    t, ops, m, n = bench.serve_stream(300, 1e7, 3)
+    reqs = [(int(ops[i]), gb.FORM_BF16 if (ops[i] == 0 and i % 2) else gb.FORM_F32, int(m[i]), int(n[i]), 1.0,
+             3 * 1000003 + i) for i in range(300)]
+    small = [i for i in range(300) if int(m[i]) * int(n[i]) <= 1 << 23]
+    picks = set()
+    for kind in (gb.REQ_GEMV, gb.REQ_DOT, gb.REQ_GER):
+        picks |= set([i for i in small if reqs[i][0] == kind][:3])
+    outs = {}
+    with gb.Engine(64 << 30, streams=4, max_inflight=16384, max_step_requests=512) as e:
+        t0 = e.now_ns() + 100_000_000
+        for i, (op, form, mi, ni, alpha, seed) in enumerate(reqs):
+            out = None
+            if i in picks:
+                out = torch.empty(out_elems(op, mi, ni), dtype=torch.float32, pin_memory=True)
+                outs[i] = out
+            assert e.submit(i, op, mi, ni, alpha, seed, out, arrival_ns=int(t0 + t[i]), form=form) == gb.GB_OK
+        assert e.drain(300000) == gb.GB_OK
+        done = e.poll()
+        stats = e.stats()
+    assert len(done) == 300 and all(c["status"] == gb.GB_OK for c in done)
+    assert stats["bytes_peak"] <= 64 << 30
+    assert len(outs) >= 7
+    for i, out in outs.items():
+        check(reqs[i], out.numpy())

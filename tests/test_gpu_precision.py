@@ -173,3 +173,42 @@ def test_rows_scaled_log_uniform_error_budget(fmt, bound):
     if fmt == "e4m3":
         floor = (np.abs(Ah).max(axis=1) / 448.0) * 2.0 ** -10 * np.abs(xh.astype(np.float64)).sum()
     assert np.all(np.abs(got - want) <= bound * scale + floor + TOL * scale)
+
+
+@pytest.mark.parametrize("fmt,bound", [("bf16", 2.0 ** -9), ("e4m3", 2.0 ** -4)])
+def test_full_size_32768_sampled_rows(fmt, bound):
+    """The benchmark's reduced-precision workload and launch: A 32768 x 32768
+    (N(0,1), rows scaled by 10^U[-3,3]) quantised on the GPU, one GEMV; 48
+    seeded rows against the FP64 oracle on their decoded codes (kernel
+    arithmetic, TOL) and on the FP32 master (quantisation bound)."""
+    m = n = 32768
+    A = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    synth.fill_normal_rows(A, 10, 1, -3.0, 3.0)
+    xh = synth.uniform(n, 10, 3, np.float32)
+    c0 = synth.uniform(m, 10, 4, np.float32)
+    rows = np.unique(synth.integers(48, 10, 5, 0, m - 1, np.int64))
+    idx = torch.from_numpy(rows).cuda()
+    Ar = A[idx].cpu().numpy()
+    Q, s = gb.quantize(A, fmt)
+    del A
+    c = dev(c0)
+    gb.gemv_q(Q, s, dev(xh), c, 0.5, n=n)
+    got = c[idx].cpu().numpy().astype(np.float64)
+    Qr = Q[idx].cpu().numpy()
+    if fmt == "bf16":
+        deq = oracle.bf16_decode(Qr.view(np.uint16)[:, :n].ravel()).astype(np.float64).reshape(-1, n)
+    else:
+        deq = oracle.e4m3_decode(Qr[:, :n].ravel()).reshape(-1, n) * s[idx].cpu().numpy().astype(np.float64)[:, None]
+    k = rows.size
+    c0r = c0[rows]
+    want_q = oracle.gemv(0, k, n, 0.5, deq.ravel(), n, xh, c0r)
+    scale_q = oracle.gemv_scale(0, k, n, 0.5, deq.ravel(), n, xh, c0r)
+    assert np.max(np.abs(got - want_q) / scale_q) <= TOL
+    want = oracle.gemv(0, k, n, 0.5, Ar.ravel(), n, xh, c0r)
+    scale = oracle.gemv_scale(0, k, n, 0.5, Ar.ravel(), n, xh, c0r)
+    floor = 0.0
+    if fmt == "e4m3":
+        floor = 0.5 * (np.abs(Ar).max(axis=1) / 448.0) * 2.0 ** -10 * np.abs(xh.astype(np.float64)).sum()
+    assert np.all(np.abs(got - want) <= bound * scale + floor + TOL * scale)
+    del Q, s
+    torch.cuda.empty_cache()
