@@ -11,6 +11,8 @@
 //   block per (row group, chunk) unit, consecutive units per block); products
 //   are FP32 fmas in chains of at most 32, folded into a compensated FP32 sum
 //   (TwoSum), then a fixed-order block sum.
+#include <type_traits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -122,7 +124,7 @@ __device__ __forceinline__ void unpack4(const uint4& w, int k, float& f0, float&
 // are FP32 fmas in chains of at most 32, folded into a compensated FP32 sum,
 // then a fixed-order block sum; a group's missing rows (past m) re-read row
 // m-1 and are dropped.
-template <int FMT, int R, int U, int MINB>
+template <int FMT, int R, int U, int MINB, bool OFF32>
 __global__ void __launch_bounds__(kThreads, MINB)
     gemv_q_kernel(int64_t m, int64_t n, float alpha, const unsigned char* __restrict__ Q,
                   int64_t ldq_bytes, const float* __restrict__ scales, const float* __restrict__ x,
@@ -145,9 +147,20 @@ __global__ void __launch_bounds__(kThreads, MINB)
     const int64_t k0 = (int64_t)s * KC;
     const int64_t k1 = (k0 + KC < n) ? k0 + KC : n;
     const int64_t kv1 = k0 + ((k1 - k0) / PER) * PER;
-    const unsigned char* Qr[R];
+    // the group's rows: 32-bit offsets from its first row when they fit
+    // (fewer registers), else pointers
+    const unsigned char* Q0 = Q + row0 * ldq_bytes;
+    typename std::conditional<OFF32, unsigned, const unsigned char*>::type rp[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) Qr[r] = Q + (row0 + r < m ? row0 + r : m - 1) * ldq_bytes;
+    for (int r = 0; r < R; ++r) {
+      const int64_t d = ((row0 + r < m ? row0 + r : m - 1) - row0) * ldq_bytes;
+      if constexpr (OFF32) rp[r] = (unsigned)d;
+      else rp[r] = Q0 + d;
+    }
+    auto Qrow = [&](int r) -> const unsigned char* {
+      if constexpr (OFF32) return Q0 + rp[r];
+      else return rp[r];
+    };
 
     float acc[R], hi[R], lo[R];
 #pragma unroll
@@ -161,7 +174,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
       for (int q = 0; q < U; ++q)
 #pragma unroll
         for (int r = 0; r < R; ++r)
-          qp[q][r] = __ldcs(reinterpret_cast<const uint4*>(Qr[r] + (j + q * STEP) * EB));
+          qp[q][r] = __ldcs(reinterpret_cast<const uint4*>(Qrow(r) + (j + q * STEP) * EB));
 #pragma unroll
       for (int q = 0; q < U; ++q) {
 #pragma unroll
@@ -193,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
     for (; j < kv1; j += STEP) {  // remaining whole packs, one at a time
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const uint4 qv = __ldcs(reinterpret_cast<const uint4*>(Qr[r] + j * EB));
+        const uint4 qv = __ldcs(reinterpret_cast<const uint4*>(Qrow(r) + j * EB));
         float a2 = 0.f;
 #pragma unroll
         for (int k = 0; k < PER / 4; ++k) {
@@ -215,8 +228,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
       const float xj = __ldg(x + jj);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const float qv = FMT == 0 ? bf16_bits_to_float(reinterpret_cast<const uint16_t*>(Qr[r])[jj])
-                                  : e4m3_bits_to_float(Qr[r][jj]);
+        const float qv = FMT == 0 ? bf16_bits_to_float(reinterpret_cast<const uint16_t*>(Qrow(r))[jj])
+                                  : e4m3_bits_to_float(Qrow(r)[jj]);
         acc[r] = __fmaf_rn(qv, xj, acc[r]);
       }
     }
@@ -282,14 +295,18 @@ int gemv_q_launch(int fmt, int64_t m, int64_t n, float alpha, const void* Q, int
                   const float* scales, const float* x, float* c, const Split& sp, int64_t kc,
                   int64_t units, cudaStream_t st) {
   const unsigned char* q = static_cast<const unsigned char*>(Q);
+  const int64_t ldq_bytes = ldq * (fmt == 0 ? 2 : 1);
+  const bool off32 = (kQuantRows[fmt] - 1) * ldq_bytes <= (int64_t)UINT32_MAX;
+  auto go = [&](auto kern) {
+    const int grid = grid_size((const void*)kern, units);
+    kern<<<grid, kThreads, 0, st>>>(m, n, alpha, q, ldq_bytes, scales, x, c, sp, kc, units);
+  };
   if (fmt == 0) {
-    auto kern = gemv_q_kernel<0, kQuantRows[0], kQuantPacks[0], kQuantMinBlocks[0]>;
-    const int grid = grid_size((const void*)kern, units);
-    kern<<<grid, kThreads, 0, st>>>(m, n, alpha, q, ldq * 2, scales, x, c, sp, kc, units);
+    if (off32) go(gemv_q_kernel<0, kQuantRows[0], kQuantPacks[0], kQuantMinBlocks[0], true>);
+    else go(gemv_q_kernel<0, kQuantRows[0], kQuantPacks[0], kQuantMinBlocks[0], false>);
   } else {
-    auto kern = gemv_q_kernel<1, kQuantRows[1], kQuantPacks[1], kQuantMinBlocks[1]>;
-    const int grid = grid_size((const void*)kern, units);
-    kern<<<grid, kThreads, 0, st>>>(m, n, alpha, q, ldq, scales, x, c, sp, kc, units);
+    if (off32) go(gemv_q_kernel<1, kQuantRows[1], kQuantPacks[1], kQuantMinBlocks[1], true>);
+    else go(gemv_q_kernel<1, kQuantRows[1], kQuantPacks[1], kQuantMinBlocks[1], false>);
   }
   return 0;
 }
