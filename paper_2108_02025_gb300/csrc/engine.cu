@@ -287,7 +287,9 @@ struct gb_engine {
 
   // worker-only state
   std::deque<Req*> admitted;
-  int64_t inflight = 0, inflight_peak = 0, steps = 0, steps_inflight_peak = 0;
+  int64_t inflight = 0;
+  // written by the worker, read by gb_engine_stats_get
+  std::atomic<int64_t> inflight_peak{0}, steps{0}, steps_inflight_peak{0};
   std::atomic<int64_t> admitted_count{0};
   std::atomic<size_t> bytes_in_use{0}, bytes_peak{0};
   std::thread worker;
@@ -377,7 +379,7 @@ bool gb_engine::admit() {
     pending.pop_front();
     ++inflight;
     ++admitted_count;
-    inflight_peak = std::max(inflight_peak, inflight);
+    if (inflight > inflight_peak.load()) inflight_peak = inflight;
     any = true;
   }
   bytes_in_use = arena.used();
@@ -513,7 +515,7 @@ bool gb_engine::launch() {
   admitted.erase(admitted.begin(), admitted.begin() + (long)k);
   s->index = steps++;
   s->busy = true;
-  steps_inflight_peak = std::max<int64_t>(steps_inflight_peak, busy + 1);
+  if (busy + 1 > steps_inflight_peak.load()) steps_inflight_peak = busy + 1;
   const int64_t t = now_ns();
   size_t bytes = 0;
   for (Req* q : s->reqs) {
@@ -693,9 +695,9 @@ int gb_engine_stats_get(gb_engine* e, gb_engine_stats* out) {
   out->admitted = e->admitted_count.load();
   out->completed = e->completed;
   out->failed = e->failed;
-  out->steps = e->steps;
-  out->inflight_peak = e->inflight_peak;
-  out->steps_inflight_peak = e->steps_inflight_peak;
+  out->steps = e->steps.load();
+  out->inflight_peak = e->inflight_peak.load();
+  out->steps_inflight_peak = e->steps_inflight_peak.load();
   out->bytes_in_use = e->bytes_in_use.load();
   out->bytes_peak = e->bytes_peak.load();
   out->budget_bytes = e->cfg.budget_bytes;
