@@ -214,7 +214,7 @@ __device__ __noinline__ void multi_split_finish(const Split sp, int64_t grp, int
 // rows (past m) re-read row m-1 and are dropped.  Block b takes the units
 // [b*units/G, (b+1)*units/G); with S > 1 chunks the block that finishes a
 // group sums each row's S partials in chunk order (one counter per group).
-template <int R, int U, int D>
+template <int R, int U, int D, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, kRowMultiB)
     gemv_row_multi_f64_kernel(int64_t m, int64_t n, double alpha, const double* __restrict__ A, int64_t lda,
                               const double* __restrict__ x, double* __restrict__ c, const Split sp,
@@ -227,16 +227,16 @@ __global__ void __launch_bounds__(kThreads, kRowMultiB)
   __shared__ double red[R][kThreads / 32];
   __shared__ int flag;
 
-  const int S = sp.S;
+  const int S = SPLIT ? sp.S : 1;
   const int64_t u0 = units * blockIdx.x / gridDim.x;
   const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
   const int64_t jlast = (int64_t)(31 - (threadIdx.x & 31)) * V;
   for (int64_t u = u0; u < u1; ++u) {
-    const int64_t grp = u / S;
-    const int s = (int)(u - grp * S);
+    const int64_t grp = SPLIT ? u / S : u;
+    const int s = SPLIT ? (int)(u - grp * S) : 0;
     const int64_t row0 = grp * R;
-    const int64_t k0 = (int64_t)s * KC;
-    const int64_t k1 = (k0 + KC < n) ? k0 + KC : n;
+    const int64_t k0 = SPLIT ? (int64_t)s * KC : 0;
+    const int64_t k1 = SPLIT ? ((k0 + KC < n) ? k0 + KC : n) : n;
     const int64_t kv1 = k0 + ((k1 - k0) / V) * V;
     const double* Ar[R];
 #pragma unroll
@@ -344,12 +344,12 @@ __global__ void __launch_bounds__(kThreads, kRowMultiB)
 #pragma unroll
       for (int w = 0; w < kThreads / 32; ++w) t = t + red[threadIdx.x][w];
     }
-    if (S == 1) {
+    if constexpr (!SPLIT) {
       if (mine) c[row] = update(c[row], alpha, t);
-      continue;
+    } else {
+      if (mine) sp.part[(int64_t)s * m + row] = t;
+      multi_split_finish(sp, grp, row0, R, m, alpha, c, red[0], &flag);
     }
-    if (mine) sp.part[(int64_t)s * m + row] = t;
-    multi_split_finish(sp, grp, row0, R, m, alpha, c, red[0], &flag);
   }
 }
 
@@ -538,9 +538,12 @@ template <typename T, int V, bool LONG>
 int launch_long(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
   if constexpr (sizeof(T) == 8) {
     if (p.multi) {
-      auto kern = gemv_row_multi_f64_kernel<kRowMultiR, kRowMultiU, kRowMultiD>;
-      const int grid = grid_size((const void*)kern, p.units);
-      kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c, p.split, p.kc, p.units);
+      auto go = [&](auto kern) {
+        const int grid = grid_size((const void*)kern, p.units);
+        kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c, p.split, p.kc, p.units);
+      };
+      if (p.split.S > 1) go(gemv_row_multi_f64_kernel<kRowMultiR, kRowMultiU, kRowMultiD, true>);
+      else go(gemv_row_multi_f64_kernel<kRowMultiR, kRowMultiU, kRowMultiD, false>);
       return 0;
     }
   }
