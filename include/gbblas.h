@@ -233,7 +233,8 @@ int gb_gemv_e4m3(int64_t m, int64_t n, float alpha, const uint8_t *Q, int64_t ld
    products folded into a compensated FP32 sum (TwoSum), and the group adds
    its lanes by a fixed butterfly.  The parameters come from a table of
    GB_BATCH_BUCKETS entries indexed by the bucket ceil(log2(n_p)) (n_p = 1:
-   bucket 0); NULL selects the built-in table.  A row's result depends only
+   bucket 0; a BF16 item of gb_batch_plan takes the bucket of ceil(n_p / 2),
+   the same row length in 4-byte words); NULL selects the built-in table.  A row's result depends only
    on n_p and its bucket's entry: under the same table a problem gives
    bit-identical results alone or in any batch.  Problems whose A or x is not
    16-byte aligned, or whose lda is not a multiple of 4, take a scalar path

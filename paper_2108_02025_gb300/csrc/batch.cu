@@ -70,6 +70,7 @@ static_assert(sizeof(BatchProblem) == 48, "plan problem layout");
 static_assert(sizeof(BatchTile) == 48, "plan tile layout");
 
 constexpr int kTileChunk = 32;  // tile descriptors staged in shared memory at a time
+constexpr int kBatchRowsBF16 = 2;  // BF16 rows a lane group sums at once (sharing x)
 
 // ----------------------------------------------------------------- kernel ---
 
@@ -245,6 +246,97 @@ __device__ void row_ger_scalar(const BatchTile& tl, int r, int lane, int lpr) {
   for (int j = lane; j < tl.n; j += lpr) row[j] = __fmaf_rn(xr, __fmul_rn(al, __ldg(tl.x + j)), row[j]);
 }
 
+// BF16 rows r, r + step, ... (R of them, the first nr valid; the others
+// re-read row r and are dropped): each float4 of x serves all R rows, since
+// with two bytes per element a lone row would read twice its own bytes of x.
+// Every row takes exactly the steps of a lone row (same packs per lane, same
+// chain folds), so its result does not depend on its neighbours.
+template <int U, int R>
+__device__ void rows_dot_bf16(const BatchTile& tl, int r, int step, int nr, int lane, int lpr, float (&out)[R]) {
+  constexpr int PER = 8;
+  const int P = tl.n / PER;
+  const uint4* rowp[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k)
+    rowp[k] = reinterpret_cast<const uint4*>(static_cast<const unsigned short*>(tl.A) +
+                                             (int64_t)(k < nr ? r + k * step : r) * tl.lda);
+  const float4* xv = reinterpret_cast<const float4*>(tl.x);
+  float acc[R], hi[R], lo[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) acc[k] = hi[k] = lo[k] = 0.f;
+  int cnt = 0;
+  int j = lane;
+#pragma unroll 1
+  for (; j + (U - 1) * lpr < P; j += U * lpr) {
+    uint4 q[U][R];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < R; ++k) q[u][k] = __ldcs(rowp[k] + j + u * lpr);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4 x4 = __ldg(xv + (j + u * lpr) * 2 + h);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          const unsigned w0 = h ? q[u][k].z : q[u][k].x, w1 = h ? q[u][k].w : q[u][k].y;
+          acc[k] = __fmaf_rn(__uint_as_float(w0 << 16), x4.x, acc[k]);
+          acc[k] = __fmaf_rn(__uint_as_float(w0 & 0xFFFF0000u), x4.y, acc[k]);
+          acc[k] = __fmaf_rn(__uint_as_float(w1 << 16), x4.z, acc[k]);
+          acc[k] = __fmaf_rn(__uint_as_float(w1 & 0xFFFF0000u), x4.w, acc[k]);
+        }
+      }
+    cnt += PER * U;
+    if (cnt == 64) {  // PER * U divides 64
+#pragma unroll
+      for (int k = 0; k < R; ++k) fold(acc[k], hi[k], lo[k]);
+      cnt = 0;
+    }
+  }
+#pragma unroll 1
+  for (; j < P; j += lpr) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float4 x4 = __ldg(xv + j * 2 + h);
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const uint4 qq = __ldcs(rowp[k] + j);
+        const unsigned w0 = h ? qq.z : qq.x, w1 = h ? qq.w : qq.y;
+        acc[k] = __fmaf_rn(__uint_as_float(w0 << 16), x4.x, acc[k]);
+        acc[k] = __fmaf_rn(__uint_as_float(w0 & 0xFFFF0000u), x4.y, acc[k]);
+        acc[k] = __fmaf_rn(__uint_as_float(w1 << 16), x4.z, acc[k]);
+        acc[k] = __fmaf_rn(__uint_as_float(w1 & 0xFFFF0000u), x4.w, acc[k]);
+      }
+    }
+    cnt += PER;
+    if (cnt == 64) {
+#pragma unroll
+      for (int k = 0; k < R; ++k) fold(acc[k], hi[k], lo[k]);
+      cnt = 0;
+    }
+  }
+  for (int e = PER * P + lane; e < tl.n; e += lpr) {  // fewer than 8 columns, possibly fewer lanes
+    const float xe = __ldg(tl.x + e);
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+      acc[k] = __fmaf_rn(__uint_as_float((unsigned)__ldcs(reinterpret_cast<const unsigned short*>(rowp[k]) + e) << 16),
+                         xe, acc[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k) out[k] = __fadd_rn(hi[k], __fadd_rn(lo[k], acc[k]));
+}
+
+template <int R>
+__device__ __forceinline__ void rows_dot_bf16_u(const BatchTile& tl, int r, int step, int nr, int lane, int lpr,
+                                                float (&out)[R]) {
+  switch (tl.u_log2) {
+    case 0: rows_dot_bf16<1, R>(tl, r, step, nr, lane, lpr, out); break;
+    case 1: rows_dot_bf16<2, R>(tl, r, step, nr, lane, lpr, out); break;
+    default: rows_dot_bf16<4, R>(tl, r, step, nr, lane, lpr, out); break;
+  }
+}
+
 template <int KIND>
 __device__ __forceinline__ float row_dot(const BatchTile& tl, int r, int lane, int lpr) {
   if (!tl.vec) return row_dot_scalar<KIND>(tl, r, lane, lpr);
@@ -317,7 +409,22 @@ __global__ void __launch_bounds__(kThreads, 3) gemv_batch_kernel(const unsigned 
       const int wl = threadIdx.x & 31;
       // the lanes of this thread's group (aligned run of lpr lanes of the warp)
       const unsigned mask = lpr == 32 ? 0xffffffffu : ((1u << lpr) - 1u) << (wl & ~(lpr - 1));
-      for (int r = threadIdx.x >> lg; r < pb.rows; r += kThreads >> lg) {  // uniform over the group
+      const int groups = kThreads >> lg;
+      if (pb.kind == kBatchGemvBF16 && pb.vec) {  // kBatchRowsBF16 rows at a time
+        constexpr int RB = kBatchRowsBF16;
+        for (int r = threadIdx.x >> lg; r < pb.rows; r += RB * groups) {  // uniform over the group
+          const int nr = min(RB, (pb.rows - r + groups - 1) / groups);
+          float v[RB];
+          rows_dot_bf16_u<RB>(pb, r, groups, nr, lane, lpr, v);
+#pragma unroll
+          for (int k = 0; k < RB; ++k) {
+            for (int o = lpr >> 1; o > 0; o >>= 1) v[k] = __fadd_rn(v[k], __shfl_xor_sync(mask, v[k], o));
+            if (lane == 0 && k < nr) pb.c[r + k * groups] = __fmaf_rn(pb.alpha, v[k], pb.c[r + k * groups]);
+          }
+        }
+        continue;
+      }
+      for (int r = threadIdx.x >> lg; r < pb.rows; r += groups) {  // uniform over the group
         if (pb.kind == kBatchGerF32) {
           row_ger(pb, r, lane, lpr);
           continue;
@@ -357,10 +464,17 @@ inline bool tuning_ok(const gb_batch_tuning& t) {
 
 inline int elem_bytes(int kind) { return kind == kBatchGemvBF16 ? 2 : 4; }
 
+// The tuning entry follows the row's length in 4-byte words: a BF16 row of
+// n elements takes the entry of an FP32 row of ceil(n / 2).
+inline int bucket_of_item(const BatchItem& it) {
+  return bucket_of(it.kind == kBatchGemvBF16 ? (it.n + 1) / 2 : it.n);
+}
+
 // Rows per tile: about tile_bytes of the matrix, a multiple of the block's
 // row groups (256 / lpr), at least one group.
 inline int64_t tile_rows(const BatchItem& it, const gb_batch_tuning& t) {
-  const int64_t groups = kThreads / t.lanes_per_row;
+  // BF16 lane groups take kBatchRowsBF16 rows at a time
+  const int64_t groups = kThreads / t.lanes_per_row * (it.kind == kBatchGemvBF16 ? kBatchRowsBF16 : 1);
   const int64_t row_bytes = elem_bytes(it.kind) * (it.n > 0 ? it.n : 1);
   int64_t r = (int64_t)t.tile_bytes / row_bytes;
   r = r / groups * groups;
@@ -384,7 +498,7 @@ inline int64_t count_tiles(int64_t count, const BatchItem* items, const gb_batch
   int64_t T = 0;
   for (int64_t p = 0; p < count; ++p) {
     if (!active(items[p])) continue;
-    const int64_t R = tile_rows(items[p], table[bucket_of(items[p].n)]);
+    const int64_t R = tile_rows(items[p], table[bucket_of_item(items[p])]);
     T += (items[p].m + R - 1) / R;
   }
   return T;
@@ -508,7 +622,7 @@ int batch_plan(int64_t count, const BatchItem* items, const gb_batch_tuning* tab
     pb.kind = (uint8_t)it.kind;
     pb.vec = aligned16(it.A) && aligned16(it.x) && (it.lda * eb) % 16 == 0;
     if (!active(it)) continue;
-    const gb_batch_tuning& tu = table[bucket_of(it.n)];
+    const gb_batch_tuning& tu = table[bucket_of_item(it)];
     const int64_t R = tile_rows(it, tu);
     for (int64_t r0 = 0; r0 < it.m; r0 += R) {
       BatchTile& tl = tiles[t];
