@@ -70,7 +70,7 @@ static_assert(sizeof(BatchProblem) == 48, "plan problem layout");
 static_assert(sizeof(BatchTile) == 48, "plan tile layout");
 
 constexpr int kTileChunk = 32;  // tile descriptors staged in shared memory at a time
-constexpr int kBatchRowsBF16 = 2;  // BF16 rows a lane group sums at once (sharing x)
+constexpr int kBatchRowsGemv = 2;  // GEMV rows (16-byte path) a lane group sums at once, sharing x
 
 // ----------------------------------------------------------------- kernel ---
 
@@ -246,20 +246,39 @@ __device__ void row_ger_scalar(const BatchTile& tl, int r, int lane, int lpr) {
   for (int j = lane; j < tl.n; j += lpr) row[j] = __fmaf_rn(xr, __fmul_rn(al, __ldg(tl.x + j)), row[j]);
 }
 
-// BF16 rows r, r + step, ... (R of them, the first nr valid; the others
-// re-read row r and are dropped): each float4 of x serves all R rows, since
-// with two bytes per element a lone row would read twice its own bytes of x.
-// Every row takes exactly the steps of a lone row (same packs per lane, same
-// chain folds), so its result does not depend on its neighbours.
-template <int U, int R>
-__device__ void rows_dot_bf16(const BatchTile& tl, int r, int step, int nr, int lane, int lpr, float (&out)[R]) {
-  constexpr int PER = 8;
+// Rows r, r + step, ... (R of them, the first nr valid; the others re-read
+// row r and are dropped) of an FP32 or BF16 GEMV tile: each float4 of x
+// serves all R rows (with two bytes per element, a lone BF16 row would read
+// twice its own bytes of x).  Every row takes exactly the steps of a lone row
+// (same packs per lane, same chain folds), so its result does not depend on
+// its neighbours.
+template <int KIND>
+__device__ __forceinline__ void decode4(const uint4& q, int h, float (&f)[4]) {
+  if constexpr (KIND == kBatchGemvBF16) {
+    const unsigned w0 = h ? q.z : q.x, w1 = h ? q.w : q.y;
+    f[0] = __uint_as_float(w0 << 16);
+    f[1] = __uint_as_float(w0 & 0xFFFF0000u);
+    f[2] = __uint_as_float(w1 << 16);
+    f[3] = __uint_as_float(w1 & 0xFFFF0000u);
+  } else {
+    f[0] = __uint_as_float(q.x);
+    f[1] = __uint_as_float(q.y);
+    f[2] = __uint_as_float(q.z);
+    f[3] = __uint_as_float(q.w);
+  }
+}
+
+template <int KIND, int U, int R>
+__device__ void rows_dot(const BatchTile& tl, int r, int step, int nr, int lane, int lpr, float (&out)[R]) {
+  constexpr int EB = KIND == kBatchGemvBF16 ? 2 : 4;
+  constexpr int PER = 16 / EB;   // elements per 16-byte pack
+  constexpr int H = PER / 4;     // float4s of x per pack
   const int P = tl.n / PER;
   const uint4* rowp[R];
 #pragma unroll
   for (int k = 0; k < R; ++k)
-    rowp[k] = reinterpret_cast<const uint4*>(static_cast<const unsigned short*>(tl.A) +
-                                             (int64_t)(k < nr ? r + k * step : r) * tl.lda);
+    rowp[k] = reinterpret_cast<const uint4*>(static_cast<const unsigned char*>(tl.A) +
+                                             (int64_t)(k < nr ? r + k * step : r) * tl.lda * EB);
   const float4* xv = reinterpret_cast<const float4*>(tl.x);
   float acc[R], hi[R], lo[R];
 #pragma unroll
@@ -276,15 +295,16 @@ __device__ void rows_dot_bf16(const BatchTile& tl, int r, int step, int nr, int 
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float4 x4 = __ldg(xv + (j + u * lpr) * 2 + h);
+      for (int h = 0; h < H; ++h) {
+        const float4 x4 = __ldg(xv + (j + u * lpr) * H + h);
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-          const unsigned w0 = h ? q[u][k].z : q[u][k].x, w1 = h ? q[u][k].w : q[u][k].y;
-          acc[k] = __fmaf_rn(__uint_as_float(w0 << 16), x4.x, acc[k]);
-          acc[k] = __fmaf_rn(__uint_as_float(w0 & 0xFFFF0000u), x4.y, acc[k]);
-          acc[k] = __fmaf_rn(__uint_as_float(w1 << 16), x4.z, acc[k]);
-          acc[k] = __fmaf_rn(__uint_as_float(w1 & 0xFFFF0000u), x4.w, acc[k]);
+          float f[4];
+          decode4<KIND>(q[u][k], h, f);
+          acc[k] = __fmaf_rn(f[0], x4.x, acc[k]);
+          acc[k] = __fmaf_rn(f[1], x4.y, acc[k]);
+          acc[k] = __fmaf_rn(f[2], x4.z, acc[k]);
+          acc[k] = __fmaf_rn(f[3], x4.w, acc[k]);
         }
       }
     cnt += PER * U;
@@ -297,16 +317,16 @@ __device__ void rows_dot_bf16(const BatchTile& tl, int r, int step, int nr, int 
 #pragma unroll 1
   for (; j < P; j += lpr) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const float4 x4 = __ldg(xv + j * 2 + h);
+    for (int h = 0; h < H; ++h) {
+      const float4 x4 = __ldg(xv + j * H + h);
 #pragma unroll
       for (int k = 0; k < R; ++k) {
-        const uint4 qq = __ldcs(rowp[k] + j);
-        const unsigned w0 = h ? qq.z : qq.x, w1 = h ? qq.w : qq.y;
-        acc[k] = __fmaf_rn(__uint_as_float(w0 << 16), x4.x, acc[k]);
-        acc[k] = __fmaf_rn(__uint_as_float(w0 & 0xFFFF0000u), x4.y, acc[k]);
-        acc[k] = __fmaf_rn(__uint_as_float(w1 << 16), x4.z, acc[k]);
-        acc[k] = __fmaf_rn(__uint_as_float(w1 & 0xFFFF0000u), x4.w, acc[k]);
+        float f[4];
+        decode4<KIND>(__ldcs(rowp[k] + j), h, f);
+        acc[k] = __fmaf_rn(f[0], x4.x, acc[k]);
+        acc[k] = __fmaf_rn(f[1], x4.y, acc[k]);
+        acc[k] = __fmaf_rn(f[2], x4.z, acc[k]);
+        acc[k] = __fmaf_rn(f[3], x4.w, acc[k]);
       }
     }
     cnt += PER;
@@ -316,24 +336,23 @@ __device__ void rows_dot_bf16(const BatchTile& tl, int r, int step, int nr, int 
       cnt = 0;
     }
   }
-  for (int e = PER * P + lane; e < tl.n; e += lpr) {  // fewer than 8 columns, possibly fewer lanes
+  for (int e = PER * P + lane; e < tl.n; e += lpr) {  // fewer than PER columns, possibly fewer lanes
     const float xe = __ldg(tl.x + e);
 #pragma unroll
     for (int k = 0; k < R; ++k)
-      acc[k] = __fmaf_rn(__uint_as_float((unsigned)__ldcs(reinterpret_cast<const unsigned short*>(rowp[k]) + e) << 16),
-                         xe, acc[k]);
+      acc[k] = __fmaf_rn(Row<KIND>::elem(rowp[k], e), xe, acc[k]);
   }
 #pragma unroll
   for (int k = 0; k < R; ++k) out[k] = __fadd_rn(hi[k], __fadd_rn(lo[k], acc[k]));
 }
 
-template <int R>
-__device__ __forceinline__ void rows_dot_bf16_u(const BatchTile& tl, int r, int step, int nr, int lane, int lpr,
-                                                float (&out)[R]) {
+template <int KIND, int R>
+__device__ __forceinline__ void rows_dot_u(const BatchTile& tl, int r, int step, int nr, int lane, int lpr,
+                                           float (&out)[R]) {
   switch (tl.u_log2) {
-    case 0: rows_dot_bf16<1, R>(tl, r, step, nr, lane, lpr, out); break;
-    case 1: rows_dot_bf16<2, R>(tl, r, step, nr, lane, lpr, out); break;
-    default: rows_dot_bf16<4, R>(tl, r, step, nr, lane, lpr, out); break;
+    case 0: rows_dot<KIND, 1, R>(tl, r, step, nr, lane, lpr, out); break;
+    case 1: rows_dot<KIND, 2, R>(tl, r, step, nr, lane, lpr, out); break;
+    default: rows_dot<KIND, 4, R>(tl, r, step, nr, lane, lpr, out); break;
   }
 }
 
@@ -410,12 +429,13 @@ __global__ void __launch_bounds__(kThreads, 3) gemv_batch_kernel(const unsigned 
       // the lanes of this thread's group (aligned run of lpr lanes of the warp)
       const unsigned mask = lpr == 32 ? 0xffffffffu : ((1u << lpr) - 1u) << (wl & ~(lpr - 1));
       const int groups = kThreads >> lg;
-      if (pb.kind == kBatchGemvBF16 && pb.vec) {  // kBatchRowsBF16 rows at a time
-        constexpr int RB = kBatchRowsBF16;
+      if (pb.kind != kBatchGerF32 && pb.vec) {  // kBatchRowsGemv rows at a time
+        constexpr int RB = kBatchRowsGemv;
         for (int r = threadIdx.x >> lg; r < pb.rows; r += RB * groups) {  // uniform over the group
           const int nr = min(RB, (pb.rows - r + groups - 1) / groups);
           float v[RB];
-          rows_dot_bf16_u<RB>(pb, r, groups, nr, lane, lpr, v);
+          if (pb.kind == kBatchGemvBF16) rows_dot_u<kBatchGemvBF16, RB>(pb, r, groups, nr, lane, lpr, v);
+          else rows_dot_u<kBatchGemvF32, RB>(pb, r, groups, nr, lane, lpr, v);
 #pragma unroll
           for (int k = 0; k < RB; ++k) {
             for (int o = lpr >> 1; o > 0; o >>= 1) v[k] = __fadd_rn(v[k], __shfl_xor_sync(mask, v[k], o));
@@ -473,8 +493,8 @@ inline int bucket_of_item(const BatchItem& it) {
 // Rows per tile: about tile_bytes of the matrix, a multiple of the block's
 // row groups (256 / lpr), at least one group.
 inline int64_t tile_rows(const BatchItem& it, const gb_batch_tuning& t) {
-  // BF16 lane groups take kBatchRowsBF16 rows at a time
-  const int64_t groups = kThreads / t.lanes_per_row * (it.kind == kBatchGemvBF16 ? kBatchRowsBF16 : 1);
+  // GEMV lane groups take kBatchRowsGemv rows at a time
+  const int64_t groups = kThreads / t.lanes_per_row * (it.kind == kBatchGerF32 ? 1 : kBatchRowsGemv);
   const int64_t row_bytes = elem_bytes(it.kind) * (it.n > 0 ? it.n : 1);
   int64_t r = (int64_t)t.tile_bytes / row_bytes;
   r = r / groups * groups;
