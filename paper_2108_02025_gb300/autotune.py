@@ -13,6 +13,13 @@ The result is a JSON table {"buckets": {b: [lanes, packs, tile_bytes]}, ...}
 with the measured GB/s of the winner and of the built-in entry; the binding
 (``load_tuning``) reads it from ``batch_tuning.json`` beside this file.
 
+With --mix N the table is tuned on a whole mixed batch instead: N problems
+drawn like the batched benchmark's (m, n log-uniform in [32, 8192]) but
+with another seed, starting from the current table, one bucket at a time
+in order of its share of the bytes, keeping a candidate only when the whole
+batch gets at least 0.5% faster (buckets interact through the load balance
+of the shared launch, which a per-bucket batch does not see).
+
 Tuning changes the summation order of a row (lanes per row, packs per
 iteration), so results are bit-reproducible for a fixed table, and every
 candidate stays within the FP32 tolerance of the oracle (the GPU tests run
@@ -131,6 +138,47 @@ def tune(lo=5, hi=13, gbytes=1.0, reps=5, seed=0, log=print):
     return out
 
 
+def tune_mix(count=4096, seed=1, reps=3, passes=1, start=None, log=print):
+    """Coordinate descent on a mixed batch: the batched benchmark's recipe
+    (m, n log-uniform in [32, 8192]) drawn with another seed, timed whole.
+    Buckets are visited by their share of the batch's bytes, and a bucket's
+    entry changes only when the whole batch gets at least 0.5% faster."""
+    import numpy as np
+    import torch
+    import bench
+    import paper_2108_02025_gb300 as gb
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    wl = bench.BatchWorkload(dev, count=count, seed=seed)
+    table = gb.tuning_table() if start is None else start
+    entries = {b: (table[b].lanes_per_row, table[b].packs_per_iter, table[b].tile_bytes)
+               for b in range(gb.BATCH_BUCKETS)}
+    buckets = np.array([max(0, int(np.ceil(np.log2(max(int(v), 1))))) for v in wl.n])
+    weight = {int(b): int((wl.m * wl.n)[buckets == b].sum()) for b in np.unique(buckets)}
+    order = sorted(weight, key=lambda b: -weight[b])
+    best_t = time_table(wl.problems, gb.tuning_table(entries), stream, reps)
+    t_start = best_t
+    log(f"mix of {count} problems: start {best_t * 1e3:.3f} ms")
+    for _ in range(passes):
+        for b in order:
+            for cand in candidates(b):
+                if cand == entries[b]:
+                    continue
+                trial = dict(entries)
+                trial[b] = cand
+                t = time_table(wl.problems, gb.tuning_table(trial), stream, reps)
+                if t < best_t * 0.995:
+                    best_t, entries = t, trial
+            log(f"bucket {b}: {entries[b]}, batch {best_t * 1e3:.3f} ms")
+    out = {"buckets": {str(b): list(entries[b]) for b in order},
+           "mix": {"problems": count, "seed": seed, "bytes": wl.bytes, "start_ms": round(t_start * 1e3, 3),
+                   "tuned_ms": round(best_t * 1e3, 3)},
+           "device": torch.cuda.get_device_name(dev)}
+    del wl
+    torch.cuda.empty_cache()
+    return out
+
+
 def main(argv=None):
     import paper_2108_02025_gb300 as gb
     p = argparse.ArgumentParser(description="autotune the batched GEMV tiling table")
@@ -139,9 +187,14 @@ def main(argv=None):
     p.add_argument("--hi", type=int, default=13)
     p.add_argument("--gb", type=float, default=1.0, help="GB of A per bucket's batch")
     p.add_argument("--reps", type=int, default=5)
+    p.add_argument("--mix", type=int, default=0,
+                   help="tune on a mixed batch of this many problems (coordinate descent) instead of per bucket")
     args = p.parse_args(argv)
     t0 = time.time()
-    out = tune(args.lo, args.hi, args.gb, args.reps)
+    if args.mix:
+        out = tune_mix(args.mix, reps=3, start=gb.load_tuning())
+    else:
+        out = tune(args.lo, args.hi, args.gb, args.reps)
     out["seconds"] = round(time.time() - t0, 1)
     with open(args.out, "w") as f:
         json.dump(out, f, indent=1, sort_keys=True)
