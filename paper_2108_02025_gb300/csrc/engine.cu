@@ -243,6 +243,8 @@ struct Req {
   unsigned char* ptr(int i) const { return base + f.p[i].off; }
 };
 
+constexpr int64_t kSpinNs = 200000;  // the worker polls instead of sleeping this close to an arrival
+
 int64_t now_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(
              std::chrono::steady_clock::now().time_since_epoch())
@@ -553,15 +555,18 @@ void gb_engine::run() {
     std::unique_lock<std::mutex> lk(mu);
     if (stop && pending.empty() && admitted.empty() && !busy) break;
     if (progress) continue;
-    if (busy) {  // steps on the GPU: poll their events again shortly
+    // Steps on the GPU, or an arrival due within kSpinNs: poll again at
+    // once (a timed sleep overshoots by tens of microseconds, which would
+    // add to every request's latency); otherwise sleep until shortly before
+    // the next arrival, or until a submission.
+    const int64_t wait = pending.empty() ? INT64_MAX : pending.front()->r.arrival_ns - now_ns();
+    if (busy || wait <= kSpinNs) {
       lk.unlock();
-      std::this_thread::sleep_for(std::chrono::microseconds(5));
+      std::this_thread::yield();
       continue;
     }
-    // idle: sleep until the next arrival or a submission
     if (!pending.empty()) {
-      const int64_t wait = pending.front()->r.arrival_ns - now_ns();
-      if (wait > 0) cv_work.wait_for(lk, std::chrono::nanoseconds(std::min<int64_t>(wait, 1000000)));
+      cv_work.wait_for(lk, std::chrono::nanoseconds(std::min<int64_t>(wait - kSpinNs, 1000000)));
     } else if (!stop) {
       cv_work.wait_for(lk, std::chrono::milliseconds(1));
     }
