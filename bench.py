@@ -348,15 +348,25 @@ def time_sample(work):
 
 # -------------------------------------------------------------- roofline --
 
+def code_of(text: str) -> str:
+    """C/C++ source without its comments and blank space, so that a change
+    of comments alone does not count as a change of the kernel."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def source_sha(files=None):
-    """sha256 of the kernel sources (all of csrc/, or the named files)."""
+    """sha256 of the code of the kernel sources (all of csrc/, or the named
+    files), comments left out."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2108_02025_gb300", "csrc")
     names = sorted(files) if files else sorted(f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h")))
     for f in names:
         h.update(f.encode())
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            h.update(code_of(fh.read()).encode())
     return h.hexdigest()
 
 

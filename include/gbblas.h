@@ -54,11 +54,15 @@
  *
  * Rounding.  IEEE round-to-nearest everywhere, no flush to zero.  GER is one
  * fma per element and therefore exact to the last bit.  GEMV and DOT
- * reassociate the sum (any order is a valid reading of the definitions);
- * FP64 sums accumulate in FP64, FP32 GEMV accumulates in FP32 for at most 64
- * terms at a time before moving the partial into FP64, FP32 DOT uses a
- * compensated FP32 dot product per thread and FP64 above that, and the last
- * reduction of DOT is always FP64.
+ * reassociate the sum (any order is a valid reading of the definitions):
+ * FP32 GEMV sums at most 64 products in one FP32 chain and adds the chains
+ * with a compensated FP32 sum (TwoSum), split partials in FP64; FP32 DOT
+ * uses a compensated FP32 dot product per thread and FP64 above that; FP64
+ * GEMV and DOT form part of their products in FP64 and part exactly with
+ * FP32 instructions (each operand cut into two FP32 parts, TwoProduct,
+ * TwoSum into an FP32 pair folded into the FP64 sum every 32 products or
+ * fewer; each such product within 2^-45 of exact), operands outside
+ * 2^-30 <= |v| < 2^31 always in FP64; the last reduction of DOT is FP64.
  *
  * Fault injection (host side, for failure tests): GB_FAULT_INJECT=<op>:<k>
  * with <op> one of gemv, dot, ger makes the k-th call (1-based, counted per

@@ -27,8 +27,9 @@ constexpr int kRowLongU = 4;     // packs in flight per thread, long-row kernel 
 constexpr int kRowLongU64 = 8;   // the same for FP64
 constexpr int kRowLongD64 = 4;   // of those, packs formed on the FP64 pipe (the rest emulated)
 constexpr int kRowLongB64 = 4;   // FP64 long-row kernel: resident blocks per SM budgeted for
-// FP64 long rows without a split: R rows per unit share each load and split
-// of x; U packs per row in flight, D of them on the FP64 pipe; B blocks/SM.
+// FP64 long rows (at least kRowMultiMinRows): R rows per unit share each load
+// and cut of x; U packs per row in flight, D of them on the FP64 pipe; B
+// resident blocks per SM.
 constexpr int kRowMultiR = 2;
 constexpr int kRowMultiU = 4;
 constexpr int kRowMultiD = 1;

@@ -92,3 +92,11 @@ def test_reference_arm_prints_contract_line():
         assert k in line, k
     assert line["impl"] == "reference" and line["unit"] == "GB/s" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_source_sha_ignores_comments_only():
+    import bench
+    a = "int f(int x) {  // twice\n  return 2 * x; /* doubled */\n}\n"
+    b = "/* header */\nint f(int x) {\n\n  return 2 * x;\n}  // end\n"
+    c = "int f(int x) { return 3 * x; }"
+    assert bench.code_of(a) == bench.code_of(b) != bench.code_of(c)
