@@ -174,7 +174,23 @@ struct RowShape {
   SplitShape sp;
 };
 
-inline RowShape row_shape(size_t e, bool vec, int64_t m, int64_t n) {
+// al: 2 = A rows and x 16-byte aligned (16-byte packs), 1 = x 16-byte
+// aligned and A element-aligned but its rows not on 16 bytes (long rows are
+// read realigned), 0 = anything else (scalar loads).
+inline RowShape row_shape(size_t e, int al, int64_t m, int64_t n) {
+  const bool vec = al == 2;
+  if (al == 1 && cdiv(n, 16 / (int64_t)e) > 256) {  // long rows, realigned packs
+    RowShape r{};
+    const int64_t V = 16 / (int64_t)e;
+    const int64_t quantum = 256 * V;
+    r.kind = GemvPlan::kRowShift;
+    SplitShape s = block_split(m, n, quantum * kRowLongU, quantum, e, kWaveBlocks, kRowMinUnits);
+    s.G = s.S;  // one counter per row, as the long-row kernel
+    s.NG = 1;
+    r.sp = s;
+    r.long_chain = e == 4 && cdiv(s.kc, 256 * V) * V > 64;
+    return r;
+  }
   const int64_t V = vec ? 16 / (int64_t)e : 1;
   RowShape r{};
   const int64_t packs = cdiv(n, V);
@@ -266,8 +282,8 @@ inline size_t dot_bytes(int64_t blocks) {
 // are sized and the larger is reported.
 size_t gemv_ws(size_t e, int layout, int64_t m, int64_t n) {
   size_t b = 0;
-  for (int vec = 0; vec < 2; ++vec) {
-    const SplitShape s = layout == GB_ROW_MAJOR ? row_shape(e, vec, m, n).sp : col_shape(e, vec, m, n).sp;
+  for (int al = 0; al < 3; ++al) {
+    const SplitShape s = layout == GB_ROW_MAJOR ? row_shape(e, al, m, n).sp : col_shape(e, al == 2, m, n).sp;
     const size_t w = split_bytes(s, m);
     if (w > b) b = w;
   }
@@ -358,12 +374,13 @@ int gemv(int layout, int64_t m, int64_t n, T alpha, const T* A, int64_t lda, con
 
   const int64_t V = 16 / (int64_t)e;
   const bool vec = aligned16(A) && aligned16(x) && lda % V == 0;
+  const int al = vec ? 2 : (aligned16(x) && reinterpret_cast<uintptr_t>(A) % e == 0) ? 1 : 0;
   GemvArgs<T> a{m, n, alpha, A, lda, x, c};
   GemvPlan p{};
   p.vec = vec;
   SplitShape s;
   if (layout == GB_ROW_MAJOR) {
-    const RowShape r = row_shape(e, vec, m, n);
+    const RowShape r = row_shape(e, al, m, n);
     p.kind = r.kind;
     p.lpr = r.lpr;
     p.long_chain = r.long_chain;
@@ -686,8 +703,8 @@ void* noalloc_scratch() {
 // be zero when a call starts), for either pointer-alignment variant.
 size_t noalloc_ticket_bytes(int layout, int64_t m, int64_t n) {
   size_t b = 0;
-  for (int vec = 0; vec < 2; ++vec) {
-    const SplitShape s = layout == GB_ROW_MAJOR ? row_shape(8, vec, m, n).sp : col_shape(8, vec, m, n).sp;
+  for (int al = 0; al < 3; ++al) {
+    const SplitShape s = layout == GB_ROW_MAJOR ? row_shape(8, al, m, n).sp : col_shape(8, al == 2, m, n).sp;
     if (s.S <= 1) continue;
     const size_t t = ticket_bytes(s);
     if (t > b) b = t;

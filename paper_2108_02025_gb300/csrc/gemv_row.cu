@@ -206,6 +206,128 @@ __device__ __noinline__ void multi_split_finish(const Split sp, int64_t grp, int
   if (threadIdx.x == 0) sp.tickets[grp] = 0u;
 }
 
+// Row-major long rows that do not start on a 16-byte boundary (lda not a
+// multiple of the pack, or A itself offset by whole elements), x 16-byte
+// aligned.  A row is read in 16-byte packs from the aligned address below
+// it: the columns [tV, tV+V) are the last V - MIS elements of aligned pack t
+// and the first MIS of pack t+1 (both inside the row; MIS is the row's
+// offset in elements, the same for every lane), so A and x line up again;
+// the first column pack and the row's end are read element by element.
+// Units, blocks, chains and sums as in the long-row kernel; FP64 products
+// all on the FP64 pipe.
+template <typename T, int V, int MIS, int U, bool LONG>
+__device__ __forceinline__ T shift_packs(const T* __restrict__ Ab, const T* __restrict__ x, int64_t tv0,
+                                         int64_t tv1) {
+  constexpr int64_t SP = kThreads;  // packs per block pass
+  constexpr int FLUSH = LONG ? (64 / (U * V) > 0 ? 64 / (U * V) : 1) : 1 << 30;
+  T acc = T(0), hi = T(0), lo = T(0);
+  int body = 0;
+  int64_t t = tv0 + threadIdx.x;
+#pragma unroll 1
+  for (; t + (U - 1) * SP < tv1; t += U * SP) {
+    Pack<T, V> a0[U], a1[U], xp[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      a0[q] = ld_stream<T, V>(Ab + (t + q * SP) * V);
+      if constexpr (MIS > 0) a1[q] = ld_keep<T, V>(Ab + (t + q * SP + 1) * V);  // the neighbour lane's pack
+      xp[q] = ld_keep<T, V>(x + (t + q * SP) * V);
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q)
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        T a;
+        if constexpr (MIS > 0) a = v + MIS < V ? a0[q].v[v + MIS] : a1[q].v[v + MIS - V];
+        else a = a0[q].v[v];
+        acc = fma_rn(a, xp[q].v[v], acc);
+      }
+    if constexpr (LONG) {
+      if (++body == FLUSH) {
+        body = 0;
+        float e;
+        two_sum_f(hi, acc, hi, e);
+        lo = __fadd_rn(lo, e);
+        acc = T(0);
+      }
+    }
+  }
+#pragma unroll 1
+  for (; t < tv1; t += SP) {
+    const Pack<T, V> a0 = ld_stream<T, V>(Ab + t * V);
+    Pack<T, V> a1;
+    if constexpr (MIS > 0) a1 = ld_keep<T, V>(Ab + (t + 1) * V);
+    const Pack<T, V> xp = ld_keep<T, V>(x + t * V);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      T a;
+      if constexpr (MIS > 0) a = v + MIS < V ? a0.v[v + MIS] : a1.v[v + MIS - V];
+      else a = a0.v[v];
+      acc = fma_rn(a, xp.v[v], acc);
+    }
+  }
+  if constexpr (LONG) acc = hi + (lo + acc);
+  return acc;
+}
+
+template <typename T, int V, int U, bool LONG>
+__global__ void __launch_bounds__(kThreads, 4)
+    gemv_row_shift_kernel(int64_t m, int64_t n, T alpha, const T* __restrict__ A, int64_t lda,
+                          const T* __restrict__ x, T* __restrict__ c, const Split sp, int64_t KC,
+                          int64_t units) {
+  __shared__ double red_d[kThreads / 32];
+  __shared__ int flag;
+  T* red = reinterpret_cast<T*>(red_d);
+  const int S = sp.S;
+  const int64_t u0 = units * blockIdx.x / gridDim.x;
+  const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
+  for (int64_t u = u0; u < u1; ++u) {
+    const int64_t row = u / S;
+    const int s = (int)(u - row * S);
+    const int64_t k0 = (int64_t)s * KC;  // a multiple of V
+    const int64_t k1 = (k0 + KC < n) ? k0 + KC : n;
+    const T* Ar = A + row * lda;
+    const int mis = (int)((reinterpret_cast<uintptr_t>(Ar) / sizeof(T)) % V);
+    const T* Ab = Ar - mis;  // 16-byte aligned
+    // column packs read as vectors: inside [k0, k1), and (MIS > 0) pack t+1
+    // of the aligned base still inside the row, pack t not before it
+    int64_t tv0 = k0 / V, tv1 = k1 / V;
+    if (mis > 0) {
+      if (tv0 < 1) tv0 = 1;
+      const int64_t lim = (mis + n) / V - 1;
+      if (tv1 > lim) tv1 = lim;
+    }
+    if (tv1 < tv0) tv1 = tv0;
+    T acc;
+    switch (mis) {
+      case 0: acc = shift_packs<T, V, 0, U, LONG>(Ab, x, tv0, tv1); break;
+      case 1: acc = shift_packs<T, V, 1, U, LONG>(Ab, x, tv0, tv1); break;
+      case 2: acc = shift_packs<T, V, (V > 2 ? 2 : 1), U, LONG>(Ab, x, tv0, tv1); break;
+      default: acc = shift_packs<T, V, (V > 3 ? 3 : 1), U, LONG>(Ab, x, tv0, tv1); break;
+    }
+    // the columns outside the vector packs, element by element
+    for (int64_t col = k0 + threadIdx.x; col < tv0 * V && col < k1; col += kThreads)
+      acc = fma_rn(__ldcs(Ar + col), __ldg(x + col), acc);
+    for (int64_t col = (tv1 * V > k0 ? tv1 * V : k0) + threadIdx.x; col < k1; col += kThreads)
+      if (col >= tv0 * V) acc = fma_rn(__ldcs(Ar + col), __ldg(x + col), acc);
+
+    const T total = block_total<T>(acc, red);
+    if (S == 1) {
+      if (threadIdx.x == 0) c[row] = update(c[row], alpha, total);
+    } else {
+      if (threadIdx.x == 0) sp.part[(int64_t)s * m + row] = (double)total;
+      if (arrive_last(sp.tickets + row, (unsigned)S, &flag)) {
+        double p = 0.0;
+        for (int q = threadIdx.x; q < S; q += kThreads) p = __dadd_rn(p, __ldcg(sp.part + (int64_t)q * m + row));
+        const double sum = block_total<double>(p, red_d);
+        if (threadIdx.x == 0) {
+          c[row] = update_from(c[row], alpha, sum);
+          sp.tickets[row] = 0u;
+        }
+      }
+    }
+  }
+}
+
 // FP64 long rows: a unit is a group of R consecutive rows times a chunk of
 // KC columns, so each 16-byte load of x, and each cut of an x value into
 // FP32 parts for the emulated products, serves R rows; per row the first D
@@ -564,6 +686,15 @@ int launch_short(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
   return 0;
 }
 
+template <typename T, bool LONG>
+int launch_shift(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
+  constexpr int V = 16 / sizeof(T);
+  auto kern = gemv_row_shift_kernel<T, V, kRowLongU, LONG>;
+  const int grid = grid_size((const void*)kern, p.units);
+  kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c, p.split, p.kc, p.units);
+  return 0;
+}
+
 template <typename T, int LPR>
 int launch_scalar(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
   auto kern = gemv_row_scalar_kernel<T, LPR, kRowScalarRW>;
@@ -583,6 +714,12 @@ int gemv_row_launch(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
       return p.long_chain ? launch_long<T, V, true>(a, p, st) : launch_long<T, V, false>(a, p, st);
     else
       return launch_long<T, V, false>(a, p, st);
+  }
+  if (p.kind == GemvPlan::kRowShift) {
+    if constexpr (sizeof(T) == 4)
+      return p.long_chain ? launch_shift<T, true>(a, p, st) : launch_shift<T, false>(a, p, st);
+    else
+      return launch_shift<T, false>(a, p, st);
   }
   if (p.kind == GemvPlan::kRowShort) {
     switch (p.lpr) {

@@ -181,3 +181,46 @@ def test_row_major_equals_col_major_of_transpose():
     c = gpu_gemv(np.float64, COL, m, n, 1.0, np.ascontiguousarray(M.T).ravel(), m, x, c0)
     scale = oracle.gemv_scale(ROW, m, n, 1.0, M.ravel(), n, x, c0)
     assert rel_err(r, c, scale) <= 2e-12
+
+
+def gpu_gemv_offsets(dt, m, n, alpha, A, ld, x, c0, a_off):
+    """A starts a_off elements after a 256-byte boundary, x 16-byte aligned."""
+    dA = to_dev(A, a_off)
+    dx = to_dev(x, 0)
+    dc = Guarded(c0, 0)
+    code = gb.F64 if dt == np.float64 else gb.F32
+    nb = gb.gb_workspace_bytes(gb.OP_GEMV, code, ROW, m, n)
+    ws = workspace(nb)
+    f = gb.gb_dgemv if dt == np.float64 else gb.gb_sgemv
+    assert f(ROW, m, n, alpha, dA, ld, dx, dc.view, ws, nb) == gb.GB_OK
+    torch.cuda.synchronize()
+    return dc.result()
+
+
+@pytest.mark.parametrize("dt", DTYPES, ids=DT_IDS)
+@pytest.mark.parametrize("shape", [(37, 5000), (3, 200001), (600, 2049), (1, 4099), (5000, 1030)],
+                         ids=lambda s: f"{s[0]}x{s[1]}")
+def test_rows_off_16_bytes_with_aligned_x(dt, shape):
+    """Row-major A whose rows do not start on 16 bytes (lda not a multiple of
+    the pack, or A offset by whole elements) with x 16-byte aligned: the
+    realigned long-row path, every row offset, ragged ends, split rows."""
+    m, n = shape
+    V = 16 // np.dtype(dt).itemsize
+    for pad, a_off in ((1, 0), (2, 1), (3, 0), (0, 1), (V - 1, V - 1), (5, 2)):
+        A, x, c0, ld = make(dt, ROW, m, n, pad, seed=m + n + pad)
+        got = gpu_gemv_offsets(dt, m, n, -0.75, A, ld, x, c0, a_off % V)
+        want = oracle.gemv(ROW, m, n, -0.75, A, ld, x, c0)
+        scale = oracle.gemv_scale(ROW, m, n, -0.75, A, ld, x, c0)
+        err = rel_err(got, want, scale)
+        assert err <= TOL[dt], (dt, m, n, pad, a_off, err)
+
+
+@pytest.mark.parametrize("dt", DTYPES, ids=DT_IDS)
+def test_rows_off_16_bytes_integer_exact(dt):
+    m, n = 64, 30001
+    A = synth.integers((m - 1) * (n + 1) + n, 31, 1, -8, 8, dt)
+    x = synth.integers(n, 31, 2, -8, 8, dt)
+    c0 = synth.integers(m, 31, 3, -8, 8, dt)
+    got = gpu_gemv_offsets(dt, m, n, 1.0, A, n + 1, x, c0, 0)
+    want = oracle.gemv(ROW, m, n, 1.0, A, n + 1, x, c0)
+    assert np.array_equal(got.astype(np.float64), want)
