@@ -191,6 +191,14 @@ inline RowShape row_shape(size_t e, int al, int64_t m, int64_t n) {
     r.long_chain = e == 4 && cdiv(s.kc, 256 * V) * V > 64;
     return r;
   }
+  if (al == 1) {  // short rows, realigned packs (lane groups as for aligned short rows)
+    RowShape r{};
+    const int64_t packs = cdiv(n, 16 / (int64_t)e);
+    r.kind = GemvPlan::kRowShortShift;
+    r.lpr = (int)pow2_at_least(cdiv(packs, kRowShortPPL), 32);
+    r.sp = SplitShape{1, 1, 1, n, cdiv(m, 256 / r.lpr)};
+    return r;
+  }
   const int64_t V = vec ? 16 / (int64_t)e : 1;
   RowShape r{};
   const int64_t packs = cdiv(n, V);

@@ -54,7 +54,7 @@ constexpr int kQuantMinBlocks[2] = {2, 3};
 // summation order depend only on (dtype, layout, m, n) and on the pointer
 // alignment (which selects the 16-byte or the scalar variant).
 struct GemvPlan {
-  enum Kind { kRowLong, kRowShort, kRowShift, kRowScalar, kCol };
+  enum Kind { kRowLong, kRowShort, kRowShift, kRowShortShift, kRowScalar, kCol };
   Kind kind;
   bool vec;         // 16-byte packs (A, x 16-byte aligned and lda a multiple of the pack)
   bool long_chain;  // FP32 only: a thread sums more than 64 products of one row

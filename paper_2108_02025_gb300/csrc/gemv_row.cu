@@ -521,6 +521,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowShortB64 : 4)
       if (ok && p < packs) ap[k] = ld_stream<T, V>(Ar + p * V);
     }
     T acc = (ok && tail) ? __ldcs(Ar + kv1 + l) * xt : T(0);
+    if constexpr (V > 2) {  // FP32: up to 3 ragged columns, and as few as 1 or 2 lanes per row
+      if (ok)
+        for (int64_t col = kv1 + l + LPR; col < n; col += LPR) acc = fma_rn(__ldcs(Ar + col), __ldg(x + col), acc);
+    }
     if constexpr (sizeof(T) == 8) {
       // FP64: packs 0..PD-1 on the FP64 pipe, packs PD..7 with FP32
       // instructions (emu_fma, x cut once per block above) when every lane
@@ -589,6 +593,65 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowShortB64 : 4)
           for (int v = 0; v < V; ++v) acc = fma_rn(ap[k].v[v], xp.v[v], acc);
         }
       }
+    }
+    T sum;
+    if constexpr (sizeof(T) == 4) sum = group_sum_f<LPR>(acc);
+    else sum = group_sum<LPR>(acc);
+    if (ok && l == 0) c[row] = update(c[row], alpha, sum);
+  }
+}
+
+// Short rows off 16 bytes, x 16-byte aligned: the lane groups of the short
+// kernel, with each column pack realigned from aligned packs p and p+1 of
+// the row (both inside it; the row's offset MIS is per row, chosen per pack
+// by selects), the first pack and the row's end element by element.  FP64
+// products all on the FP64 pipe.
+template <typename T, int V>
+__device__ __forceinline__ T pick(const Pack<T, V>& a0, const Pack<T, V>& a1, int v, int mis) {
+  const int k = v + mis;
+  T r = a0.v[0];
+#pragma unroll
+  for (int i = 1; i < V; ++i) r = k == i ? a0.v[i] : r;
+#pragma unroll
+  for (int i = 0; i < V - 1; ++i) r = k == V + i ? a1.v[i] : r;
+  return r;
+}
+
+template <typename T, int V, int LPR>
+__global__ void __launch_bounds__(kThreads, 4)
+    gemv_row_short_shift_kernel(int64_t m, int64_t n, T alpha, const T* __restrict__ A, int64_t lda,
+                                const T* __restrict__ x, T* __restrict__ c) {
+  constexpr int GROUPS = kThreads / LPR;
+  constexpr int PMAX = 8;
+  const int l = threadIdx.x % LPR;
+  const int g = threadIdx.x / LPR;
+  const int64_t r0 = m * blockIdx.x / gridDim.x;
+  const int64_t r1 = m * (blockIdx.x + 1) / gridDim.x;
+#pragma unroll 1
+  for (int64_t base = r0; base < r1; base += GROUPS) {  // the same trips for every thread
+    const int64_t row = base + g;
+    const bool ok = row < r1;
+    const T* Ar = A + (ok ? row : r0) * lda;
+    const int mis = (int)((reinterpret_cast<uintptr_t>(Ar) / sizeof(T)) % V);
+    const T* Ab = Ar - mis;
+    const int64_t pv0 = mis > 0 ? 1 : 0;
+    int64_t pv1 = mis > 0 ? (mis + n) / V - 1 : n / V;
+    if (pv1 < pv0) pv1 = pv0;
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < PMAX; ++k) {
+      const int64_t p = (int64_t)k * LPR + l;
+      if (ok && p >= pv0 && p < pv1) {
+        const Pack<T, V> a0 = ld_stream<T, V>(Ab + p * V);
+        const Pack<T, V> a1 = ld_keep<T, V>(Ab + (p + 1) * V);
+        const Pack<T, V> xp = ld_keep<T, V>(x + p * V);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc = fma_rn(pick<T, V>(a0, a1, v, mis), xp.v[v], acc);
+      }
+    }
+    if (ok) {
+      for (int64_t col = l; col < pv0 * V && col < n; col += LPR) acc = fma_rn(__ldcs(Ar + col), __ldg(x + col), acc);
+      for (int64_t col = pv1 * V + l; col < n; col += LPR) acc = fma_rn(__ldcs(Ar + col), __ldg(x + col), acc);
     }
     T sum;
     if constexpr (sizeof(T) == 4) sum = group_sum_f<LPR>(acc);
@@ -686,6 +749,16 @@ int launch_short(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
   return 0;
 }
 
+template <typename T, int LPR>
+int launch_short_shift(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
+  constexpr int V = 16 / sizeof(T);
+  auto kern = gemv_row_short_shift_kernel<T, V, LPR>;
+  constexpr int64_t rows_per_iter = kThreads / LPR;
+  const int grid = grid_size((const void*)kern, (a.m + rows_per_iter - 1) / rows_per_iter);
+  kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c);
+  return 0;
+}
+
 template <typename T, bool LONG>
 int launch_shift(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
   constexpr int V = 16 / sizeof(T);
@@ -720,6 +793,16 @@ int gemv_row_launch(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
       return p.long_chain ? launch_shift<T, true>(a, p, st) : launch_shift<T, false>(a, p, st);
     else
       return launch_shift<T, false>(a, p, st);
+  }
+  if (p.kind == GemvPlan::kRowShortShift) {
+    switch (p.lpr) {
+      case 32: return launch_short_shift<T, 32>(a, p, st);
+      case 16: return launch_short_shift<T, 16>(a, p, st);
+      case 8: return launch_short_shift<T, 8>(a, p, st);
+      case 4: return launch_short_shift<T, 4>(a, p, st);
+      case 2: return launch_short_shift<T, 2>(a, p, st);
+      default: return launch_short_shift<T, 1>(a, p, st);
+    }
   }
   if (p.kind == GemvPlan::kRowShort) {
     switch (p.lpr) {

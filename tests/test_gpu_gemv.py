@@ -198,12 +198,14 @@ def gpu_gemv_offsets(dt, m, n, alpha, A, ld, x, c0, a_off):
 
 
 @pytest.mark.parametrize("dt", DTYPES, ids=DT_IDS)
-@pytest.mark.parametrize("shape", [(37, 5000), (3, 200001), (600, 2049), (1, 4099), (5000, 1030)],
+@pytest.mark.parametrize("shape", [(37, 5000), (3, 200001), (600, 2049), (1, 4099), (5000, 1030),
+                                   (1000, 63), (3000, 130), (257, 1021), (77, 5), (4, 1)],
                          ids=lambda s: f"{s[0]}x{s[1]}")
 def test_rows_off_16_bytes_with_aligned_x(dt, shape):
     """Row-major A whose rows do not start on 16 bytes (lda not a multiple of
     the pack, or A offset by whole elements) with x 16-byte aligned: the
-    realigned long-row path, every row offset, ragged ends, split rows."""
+    realigned long-row and short-row paths, every row offset, ragged ends,
+    split rows."""
     m, n = shape
     V = 16 // np.dtype(dt).itemsize
     for pad, a_off in ((1, 0), (2, 1), (3, 0), (0, 1), (V - 1, V - 1), (5, 2)):
@@ -224,3 +226,15 @@ def test_rows_off_16_bytes_integer_exact(dt):
     got = gpu_gemv_offsets(dt, m, n, 1.0, A, n + 1, x, c0, 0)
     want = oracle.gemv(ROW, m, n, 1.0, A, n + 1, x, c0)
     assert np.array_equal(got.astype(np.float64), want)
+
+
+@pytest.mark.parametrize("dt", DTYPES, ids=DT_IDS)
+def test_short_rows_padded_ld_ragged_end(dt):
+    """Aligned short rows (lda a multiple of the pack, n not): the ragged
+    columns past the last pack when a row has fewer lanes than ragged
+    columns (1 or 2 lanes per row, FP32)."""
+    V = 16 // np.dtype(dt).itemsize
+    for n in (1, 2, 3, 5, 6, 7, 9, 14, 15, 31, 63, 127):
+        m = 700
+        ld = (n + V - 1) // V * V
+        check(dt, ROW, m, n, pad=ld - n, alpha=0.5, seed=n)
