@@ -2,8 +2,10 @@
 //
 // Alg. 1 of the paper (Sec. 4.1) blocks rows by m_c, columns by n_c and
 // updates a short run of c, c(i_r : i_r + m_r), from a block of A and the
-// matching block of x (its micro-kernel).  For misaligned operands (scalar
-// loads) a warp item is TXW*V rows
+// matching block of x (its micro-kernel).  With 16-byte aligned operands a
+// block tile is TX*V rows by a chunk of columns (gemv_col_tile_kernel, up to
+// 256 row threads when the columns are few).  For misaligned operands
+// (scalar loads) a warp item is TXW*V rows
 // (each lane owns V consecutive rows, one 16-byte pack per column: the m_r
 // of the micro-kernel) by a chunk of KC columns (n_c), walked by TYW =
 // 32/TXW column lanes, so one load instruction of the warp reads TYW column

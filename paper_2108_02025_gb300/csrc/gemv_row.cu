@@ -15,9 +15,16 @@
 // * short rows (at most 256 packs): LPR lanes share a row, each holding up to
 //   8 of its packs, so a block iteration reads 256/LPR consecutive rows; the
 //   LPR lanes of a row are summed by a butterfly.
+// * FP64 long rows go in groups of two rows per unit (each load and FP32
+//   cut of x serves both); part of every FP64 row's products are formed
+//   with FP32 instructions (gb_common.cuh), since the FP64 pipe alone cannot
+//   keep up with HBM on GB300.
 // * FP32 rows are summed in FP32 throughout (chains of at most 64 products,
 //   then a compensated FP32 sum); split partials are combined in FP64.
-// * misaligned operands (no 16-byte packs): warp items of RW rows with
+// * rows that do not start on 16 bytes (odd lda, or A offset by whole
+//   elements) with x aligned: the same units, read in aligned packs and
+//   realigned to x (shift kernels below).
+// * x misaligned too (no 16-byte packs at all): warp items of RW rows with
 //   scalar loads.
 #include "gb_common.cuh"
 #include "gb_internal.h"
