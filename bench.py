@@ -610,9 +610,13 @@ def run_batched(device, stream, hbm, reps=5):
 # --------------------------------------------------------- serving leg --
 
 SERVE_WORKLOAD = ("Poisson request stream, 70% GEMV / 20% DOT / 10% GER, m and n log-uniform in "
-                  "[32, 16384], alpha 1, operands drawn on the device per request (counter-based "
-                  "generator) and resident until completion, 64 GB HBM admission budget, 4 streams")
+                  "[32, 16384], alpha 1, operands resident on the device (pools of 2^30 FP32 and "
+                  "2^30 BF16 values from the counter-based generator, filled once), each request's "
+                  "output allocated under a 64 GB HBM admission budget, 4 streams; for comparison "
+                  "the same stream with every operand drawn on the device per request")
 SERVE_BUDGET = 64 << 30
+SERVE_POOL = 1 << 30
+SERVE_POOL_SEED = 2108
 
 
 def serve_stream(count, rate, seed, lo=32, hi=16384):
@@ -628,10 +632,11 @@ def serve_stream(count, rate, seed, lo=32, hi=16384):
     return t, ops, m, n
 
 
-def serve_once(count, rate, form, seed=0, sample=8):
-    """Serve one stream; returns throughput, latency percentiles and the
-    measured error of `sample` GEMV results (numpy FP64 on the generator's
-    FP32 values, relative to sum_j |A_ij x_j| + |c0_i|)."""
+def serve_once(count, rate, form, seed=0, sample=8, pool=True):
+    """Serve one stream (operands from the resident pools, or drawn per
+    request); returns throughput, latency percentiles and the measured error
+    of `sample` GEMV results (numpy FP64 on the generator's FP32 values,
+    relative to sum_j |A_ij x_j| + |c0_i|)."""
     import numpy as np
     import torch
     import synth
@@ -641,7 +646,8 @@ def serve_once(count, rate, form, seed=0, sample=8):
     picks = set(gemv_idx[::max(1, len(gemv_idx) // sample)][:sample]) if sample > 0 else set()
     outs = {}
     with gb.Engine(SERVE_BUDGET, streams=4, max_inflight=16384, max_step_requests=512,
-                   table=gb.load_tuning()) as e:
+                   table=gb.load_tuning(), pool_elems=SERVE_POOL if pool else 0,
+                   pool_seed=SERVE_POOL_SEED) as e:
         t0 = e.now_ns() + int(0.2e9) + count * 20000   # every request is queued before the first arrives
         for i in range(count):
             out = None
@@ -650,7 +656,7 @@ def serve_once(count, rate, form, seed=0, sample=8):
                 outs[i] = out
             fi = form if ops[i] == 0 else gb.FORM_F32
             st = e.submit(i, int(ops[i]), int(m[i]), int(n[i]), 1.0, seed * 1000003 + i, out,
-                          arrival_ns=int(t0 + t[i]), form=fi)
+                          arrival_ns=int(t0 + t[i]), form=fi, pool=pool)
             if st != gb.GB_OK:
                 raise RuntimeError(f"submit {i}: {st}")
         if e.drain(600000) != gb.GB_OK:
@@ -670,9 +676,17 @@ def serve_once(count, rate, form, seed=0, sample=8):
         mi, ni = int(m[i]), int(n[i])
         ld = (ni + 7) // 8 * 8 if form == gb.FORM_BF16 else (ni + 3) // 4 * 4
         s0 = seed * 1000003 + i
-        A = synth.uniform_pairs(mi * ld, s0, 1).reshape(mi, ld)[:, :ni].astype(np.float64)
-        x = synth.uniform_pairs(ni, s0, 2).astype(np.float64)
-        c0 = synth.uniform_pairs(mi, s0, 3).astype(np.float64)
+        if pool:    # windows of the pools; the BF16 pool rounds stream 2 of the pool seed
+            def win(s, L, stream):
+                o = synth.pool_offset(s0, s, L, SERVE_POOL)
+                return synth.uniform_pairs(L, SERVE_POOL_SEED, stream, offset=o)
+            A = win(1, mi * ld, 2 if form == gb.FORM_BF16 else 1)
+            x, c0 = win(2, ni, 1), win(3, mi, 1)
+        else:
+            A = synth.uniform_pairs(mi * ld, s0, 1)
+            x, c0 = synth.uniform_pairs(ni, s0, 2), synth.uniform_pairs(mi, s0, 3)
+        A = A.reshape(mi, ld)[:, :ni].astype(np.float64)
+        x, c0 = x.astype(np.float64), c0.astype(np.float64)
         want = c0 + A @ x
         scale = np.abs(c0) + np.abs(A) @ np.abs(x)
         err = max(err, float(np.max(np.abs(out.numpy().astype(np.float64) - want) / scale)))
@@ -705,6 +719,8 @@ def run_serving(count=20000):
         out[name] = {"saturated": sat, "loads": loads}
     out["bf16_speedup_solves"] = round(out["bf16"]["saturated"]["solves_per_s"] /
                                        out["fp32"]["saturated"]["solves_per_s"], 3)
+    out["drawn_operands"] = {name: serve_once(count, 1e7, form, seed=1, pool=False)
+                             for name, form in (("fp32", gb.FORM_F32), ("bf16", gb.FORM_BF16))}
     return out
 
 

@@ -18,11 +18,12 @@
  * and fewer than max_inflight requests are admitted; a request larger than
  * the whole budget is refused at submission.  Admitted requests are
  * launched as a step on one of `streams` CUDA streams as soon as one is
- * free: one copy of the step's descriptors, one kernel that writes every
- * new operand, one persistent launch (the batched kernel of gb_sgemv_batch)
- * for all the step's GEMVs (FP32 or BF16 A), DOTs (one-row GEMVs) and GERs,
- * then the copies of the results to the requests' host buffers and an
- * event.  GEMV and DOT sums are FP32 fma chains of at most 64 products in a
+ * free: one copy of the step's descriptors, one operand kernel (it draws
+ * the operands of requests without GB_REQ_POOL, copies the initial outputs
+ * of pool requests and computes their GERs), one persistent launch (the
+ * batched kernel of gb_sgemv_batch) for all the step's GEMVs (FP32 or BF16
+ * A), DOTs (one-row GEMVs) and the GERs of drawn requests, then the copies
+ * of the results to the requests' host buffers and an event.  GEMV and DOT sums are FP32 fma chains of at most 64 products in a
  * compensated FP32 sum; GER is one fma per element.
  * Requests that arrive while steps are on the GPU are admitted and launched
  * in the next step on another stream, so steps overlap on the device.  When
@@ -39,6 +40,22 @@
  * x=2, c=3; DOT x=1, y=2, alpha=3; GER C=1, x=2, y=3.  Matrices are stored
  * row-major with the leading dimension rounded up to 4 elements (FP32) or 8
  * (BF16); element (i, j) takes index k = i * ld + j of its stream.
+ *
+ * Resident operands (GB_REQ_POOL).  An engine created with pool_elems = P
+ * > 0 places two operand pools on the device at creation, outside the
+ * budget: P FP32 values (the generator above with pool_seed, stream 1) and
+ * P BF16 values (stream 2, rounded to nearest even).  A request flagged
+ * GB_REQ_POOL reads its inputs from the pools instead of having them drawn:
+ * operand s (same stream numbers as above) of extent L_s elements (a
+ * matrix m * ld, a vector its length) starts at element
+ *     o_s = 8 * (mix(key(seed, s)) mod (floor((P - L_s) / 8) + 1))
+ * of the FP32 pool (the BF16 pool for the A of a BF16 GEMV), so
+ * element (i, j) of a matrix is pool[o_s + i * ld + j].  Only the output is
+ * allocated in the arena (GEMV: c, DOT: alpha, GER: C, m x ld): its initial
+ * value (c0, alpha0, C0) is the pool operand of stream 3, 3 and 1, copied
+ * by the step (GER computes C0 + alpha x y^T straight into the output), so
+ * the pools are never written.  A request whose operand is longer than P is
+ * refused (-2).
  *
  * Results.  `out`, when not NULL, must be page-locked host memory (for
  * example from cudaHostAlloc or a pinned tensor): GEMV writes m floats (c),
@@ -79,6 +96,7 @@ extern "C" {
 typedef enum { GB_REQ_GEMV = 0, GB_REQ_DOT = 1, GB_REQ_GER = 2 } gb_req_op;
 typedef enum { GB_FORM_F32 = 0, GB_FORM_BF16 = 1 } gb_req_form;
 typedef enum { GB_ENGINE_HOST_ONLY = 1 } gb_engine_flags;
+typedef enum { GB_REQ_POOL = 1 } gb_req_flags;
 
 typedef struct {
   size_t budget_bytes;          /* HBM admission budget, >= 1 MiB */
@@ -88,6 +106,9 @@ typedef struct {
   int32_t flags;                /* gb_engine_flags */
   double sim_bytes_per_ns;      /* host-only mode: simulated bandwidth, > 0 */
   const gb_batch_tuning *table; /* GB_BATCH_BUCKETS entries (copied), or NULL */
+  int64_t pool_elems;           /* resident operand pool: elements (0 = none, else a
+                                   multiple of 8, at most 2^40) */
+  uint64_t pool_seed;           /* generator seed of the pool */
 } gb_engine_config;
 
 typedef struct {
@@ -96,7 +117,7 @@ typedef struct {
   int32_t form;       /* gb_req_form (GEMV only; others GB_FORM_F32) */
   int64_t m, n;       /* GEMV, GER: m x n (1 <= m, n <= 2^31 - 1); DOT: n (m ignored) */
   float alpha;        /* GEMV, GER: scale (DOT: ignored) */
-  int32_t reserved;   /* 0 */
+  int32_t flags;      /* gb_req_flags */
   uint64_t seed;      /* operands from the generator with this seed */
   void *out;          /* page-locked host buffer for the result, or NULL */
   int64_t arrival_ns; /* arrival, gb_engine_now_ns clock; 0 = at submission */
@@ -116,6 +137,7 @@ typedef struct {
   int64_t inflight_peak;    /* admitted, unfinished requests, at most at once */
   int64_t steps_inflight_peak;
   size_t bytes_in_use, bytes_peak, budget_bytes;
+  size_t pool_bytes;        /* device bytes of the operand pools (outside the budget) */
 } gb_engine_stats;
 
 typedef struct gb_engine gb_engine;
@@ -126,12 +148,14 @@ int64_t gb_engine_now_ns(void);
 /* Create an engine (and start its worker thread).  Returns GB_OK and the
    handle in *out; -1 for an invalid config (NULL, a field out of range, an
    invalid table entry), -2 for out NULL, GB_ERR_CUDA if device memory, a
-   stream or the thread cannot be had (nothing is left allocated). */
+   stream or the thread cannot be had (nothing is left allocated).  With a
+   pool, creation returns once the pools are filled. */
 int gb_engine_create(const gb_engine_config *cfg, gb_engine **out);
 
 /* Queue one request.  Returns GB_OK; -1 engine NULL; -2 request NULL or a
-   field out of range (op, form, m, n, reserved, out not page-locked);
-   GB_ERR_BUDGET when its operands alone exceed the budget. */
+   field out of range (op, form, m, n, flags, out not page-locked;
+   GB_REQ_POOL without a pool or with an operand longer than the pool);
+   GB_ERR_BUDGET when its arena bytes alone exceed the budget. */
 int gb_engine_submit(gb_engine *e, const gb_request *r);
 
 /* Copy up to `max` completions (oldest first) into out; returns how many,
@@ -145,8 +169,8 @@ int gb_engine_drain(gb_engine *e, int64_t timeout_ms);
 /* Counters; -1 for an invalid argument. */
 int gb_engine_stats_get(gb_engine *e, gb_engine_stats *out);
 
-/* Device bytes a request would hold (its operands, 256-byte aligned
-   pieces); 0 for an invalid request. */
+/* Arena bytes a request would hold (its operands, or its output alone
+   with GB_REQ_POOL; 256-byte aligned pieces); 0 for an invalid request. */
 size_t gb_engine_request_bytes(const gb_request *r);
 
 /* Finish outstanding work (up to 60 s), stop the worker and free

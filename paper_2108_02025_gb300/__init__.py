@@ -379,19 +379,20 @@ GB_ERR_TIMEOUT = -105
 REQ_GEMV, REQ_DOT, REQ_GER = 0, 1, 2
 FORM_F32, FORM_BF16 = 0, 1
 ENGINE_HOST_ONLY = 1
+REQ_POOL = 1
 
 
 class EngineConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("streams", ctypes.c_int32),
                 ("max_inflight", ctypes.c_int32), ("max_step_requests", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("sim_bytes_per_ns", ctypes.c_double),
-                ("table", ctypes.c_void_p)]
+                ("table", ctypes.c_void_p), ("pool_elems", ctypes.c_int64), ("pool_seed", ctypes.c_uint64)]
 
 
 class Request(ctypes.Structure):
     _fields_ = [("id", ctypes.c_int64), ("op", ctypes.c_int32), ("form", ctypes.c_int32),
                 ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("alpha", ctypes.c_float),
-                ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64), ("out", ctypes.c_void_p),
+                ("flags", ctypes.c_int32), ("seed", ctypes.c_uint64), ("out", ctypes.c_void_p),
                 ("arrival_ns", ctypes.c_int64)]
 
 
@@ -407,7 +408,7 @@ class EngineStats(ctypes.Structure):
                 ("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("inflight_peak", ctypes.c_int64), ("steps_inflight_peak", ctypes.c_int64),
                 ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t),
-                ("budget_bytes", ctypes.c_size_t)]
+                ("budget_bytes", ctypes.c_size_t), ("pool_bytes", ctypes.c_size_t)]
 
 
 def gb_engine_now_ns() -> int:
@@ -447,14 +448,16 @@ class Engine:
 
     ``submit`` queues a request (op, m, n, alpha, seed, optional pinned host
     tensor for the result, arrival time on ``now_ns``'s clock); ``drain``
-    waits for all of them; ``poll`` returns the completions as dicts."""
+    waits for all of them; ``poll`` returns the completions as dicts.  With
+    ``pool_elems`` > 0 the engine keeps resident operand pools and requests
+    submitted with ``pool=True`` read their inputs from them."""
 
     def __init__(self, budget_bytes, streams=4, max_inflight=4096, max_step_requests=256,
-                 host_only=False, sim_bytes_per_ns=1000.0, table=None):
+                 host_only=False, sim_bytes_per_ns=1000.0, table=None, pool_elems=0, pool_seed=0):
         self.table = table
         cfg = EngineConfig(budget_bytes, streams, max_inflight, max_step_requests,
                            ENGINE_HOST_ONLY if host_only else 0, sim_bytes_per_ns,
-                           _addr(table) if table is not None else None)
+                           _addr(table) if table is not None else None, pool_elems, pool_seed)
         h = ctypes.c_void_p()
         _check(gb_engine_create(cfg, ctypes.addressof(h)), "engine_create")
         self.h = h.value
@@ -464,9 +467,10 @@ class Engine:
     def now_ns() -> int:
         return gb_engine_now_ns()
 
-    def submit(self, rid, op, m, n, alpha=1.0, seed=0, out=None, arrival_ns=0, form=FORM_F32) -> int:
+    def submit(self, rid, op, m, n, alpha=1.0, seed=0, out=None, arrival_ns=0, form=FORM_F32,
+               pool=False) -> int:
         """Returns the status (GB_OK, -2 invalid, GB_ERR_BUDGET)."""
-        r = Request(rid, op, form, m, n, alpha, 0, seed, _ptr(out), arrival_ns)
+        r = Request(rid, op, form, m, n, alpha, REQ_POOL if pool else 0, seed, _ptr(out), arrival_ns)
         st = gb_engine_submit(self.h, ctypes.addressof(r))
         if st == GB_OK and out is not None:
             self._keep[rid] = out  # the engine writes into it later
@@ -509,8 +513,8 @@ class Engine:
             pass
 
 
-def request_bytes(op, m, n, form=FORM_F32) -> int:
-    r = Request(0, op, form, m, n, 1.0, 0, 0, None, 0)
+def request_bytes(op, m, n, form=FORM_F32, pool=False) -> int:
+    r = Request(0, op, form, m, n, 1.0, REQ_POOL if pool else 0, 0, None, 0)
     return gb_engine_request_bytes(ctypes.addressof(r))
 
 

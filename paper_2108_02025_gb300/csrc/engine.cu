@@ -1,7 +1,9 @@
 // Serving engine: continuous batching of GEMV / DOT / GER requests on one
 // GPU under an HBM budget (include/gbserve.h).  Not part of the paper, whose
 // operations run one call at a time (Sec. 4); a step launches one operand
-// generator and one batched level-2 kernel (batch.cu) for all its requests.
+// kernel (operands drawn by the generator; for requests on the resident
+// pools the copies of their initial outputs and their GERs, out of place)
+// and one batched level-2 kernel (batch.cu) for all its requests.
 //
 // One worker thread owns the device side: it admits arrived requests in
 // arrival order while the arena and the in-flight cap allow, launches the
@@ -45,15 +47,25 @@ __host__ __device__ inline uint64_t sm_mix(uint64_t z) {
 
 inline uint64_t stream_key(uint64_t seed, uint64_t stream) { return sm_mix(sm_mix(seed + kG) ^ (stream * kS)); }
 
-enum FillKind : int32_t { kFillF32 = 0, kFillBF16 = 1 };
+enum SegKind : int32_t { kFillF32 = 0, kFillBF16 = 1, kCopyF32 = 2, kGerF32 = 3 };
 
-struct FillSeg {  // 32 bytes
+// One piece of a step's operand work.  Fill: count generator values into
+// dst.  Copy: dst[k] = src[k].  GER (out of place): dst = src + alpha x y^T
+// over count = rows * ld elements, row r = k / ld, column j = k % ld, one
+// fma per element with t_j = fl(alpha * y_j); columns n <= j < ld copy src.
+struct OperandSeg {  // 64 bytes
   void* dst;
-  int64_t count;  // elements
-  uint64_t key;
-  int32_t kind, pad;
+  const float* src;
+  const float* x;
+  const float* y;
+  int64_t count;  // elements written
+  uint64_t key;   // fill: generator key; GER: ld (a multiple of 4)
+  int32_t kind;
+  int32_t n;      // GER: columns
+  float alpha;    // GER
+  int32_t pad;
 };
-static_assert(sizeof(FillSeg) == 32, "fill segment layout");
+static_assert(sizeof(OperandSeg) == 64, "operand segment layout");
 
 constexpr int64_t kFillChunk = 16384;  // elements per block (a multiple of 4)
 
@@ -77,11 +89,13 @@ __device__ __forceinline__ uint16_t bf16_bits(float v) {
   return *reinterpret_cast<const uint16_t*>(&h);
 }
 
-// Block b fills chunk b - first[s] of segment s, the last s with first[s] <= b:
-// four consecutive elements (two words) per thread and step, 16-byte (FP32)
-// or 8-byte (BF16) stores; segments start 256-byte aligned.
-__global__ void __launch_bounds__(kThreads) fill_kernel(const FillSeg* __restrict__ segs,
-                                                        const int64_t* __restrict__ first, int nseg) {
+// Block b works on chunk b - first[s] of segment s, the last s with
+// first[s] <= b: four consecutive elements per thread and step, 16-byte
+// (FP32) or 8-byte (BF16) accesses.  dst and src start 16-byte aligned
+// (arena pieces 256 bytes, pool operands 32 bytes), GER rows too (ld a
+// multiple of 4), so a group of four never straddles a row.
+__global__ void __launch_bounds__(kThreads) operand_kernel(const OperandSeg* __restrict__ segs,
+                                                           const int64_t* __restrict__ first, int nseg) {
   const int64_t b = blockIdx.x;
   int lo = 0, hi = nseg - 1;
   while (lo < hi) {
@@ -89,28 +103,62 @@ __global__ void __launch_bounds__(kThreads) fill_kernel(const FillSeg* __restric
     if (first[mid] <= b) lo = mid;
     else hi = mid - 1;
   }
-  const FillSeg sg = segs[lo];
+  const OperandSeg sg = segs[lo];
   const int64_t e0 = (b - first[lo]) * kFillChunk;
   const int64_t e1 = e0 + kFillChunk < sg.count ? e0 + kFillChunk : sg.count;
-  for (int64_t e = e0 + 4 * (int64_t)threadIdx.x; e < e1; e += 4 * kThreads) {
-    float v[4];
-    pair_of(sg.key, e >> 1, v[0], v[1]);
-    pair_of(sg.key, (e >> 1) + 1, v[2], v[3]);
-    if (sg.kind == kFillF32) {
-      float* d = static_cast<float*>(sg.dst) + e;
-      if (e + 4 <= e1) {
-        *reinterpret_cast<float4*>(d) = make_float4(v[0], v[1], v[2], v[3]);
+  if (sg.kind == kFillF32 || sg.kind == kFillBF16) {
+    for (int64_t e = e0 + 4 * (int64_t)threadIdx.x; e < e1; e += 4 * kThreads) {
+      float v[4];
+      pair_of(sg.key, e >> 1, v[0], v[1]);
+      pair_of(sg.key, (e >> 1) + 1, v[2], v[3]);
+      if (sg.kind == kFillF32) {
+        float* d = static_cast<float*>(sg.dst) + e;
+        if (e + 4 <= e1) {
+          *reinterpret_cast<float4*>(d) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+          for (int q = 0; q < 4 && e + q < e1; ++q) d[q] = v[q];
+        }
       } else {
-        for (int q = 0; q < 4 && e + q < e1; ++q) d[q] = v[q];
+        uint16_t* d = static_cast<uint16_t*>(sg.dst) + e;
+        if (e + 4 <= e1) {
+          const unsigned lo2 = bf16_bits(v[0]) | ((unsigned)bf16_bits(v[1]) << 16);
+          const unsigned hi2 = bf16_bits(v[2]) | ((unsigned)bf16_bits(v[3]) << 16);
+          *reinterpret_cast<uint2*>(d) = make_uint2(lo2, hi2);
+        } else {
+          for (int q = 0; q < 4 && e + q < e1; ++q) d[q] = bf16_bits(v[q]);
+        }
       }
-    } else {
-      uint16_t* d = static_cast<uint16_t*>(sg.dst) + e;
+    }
+  } else if (sg.kind == kCopyF32) {
+    float* d = static_cast<float*>(sg.dst);
+    for (int64_t e = e0 + 4 * (int64_t)threadIdx.x; e < e1; e += 4 * kThreads) {
       if (e + 4 <= e1) {
-        const unsigned lo2 = bf16_bits(v[0]) | ((unsigned)bf16_bits(v[1]) << 16);
-        const unsigned hi2 = bf16_bits(v[2]) | ((unsigned)bf16_bits(v[3]) << 16);
-        *reinterpret_cast<uint2*>(d) = make_uint2(lo2, hi2);
+        *reinterpret_cast<float4*>(d + e) = __ldcs(reinterpret_cast<const float4*>(sg.src + e));
       } else {
-        for (int q = 0; q < 4 && e + q < e1; ++q) d[q] = bf16_bits(v[q]);
+        for (int q = 0; q < 4 && e + q < e1; ++q) d[e + q] = sg.src[e + q];
+      }
+    }
+  } else {
+    float* d = static_cast<float*>(sg.dst);
+    const int64_t ld = (int64_t)sg.key;
+    const bool narrow = sg.count <= (int64_t)UINT32_MAX;
+    for (int64_t e = e0 + 4 * (int64_t)threadIdx.x; e < e1; e += 4 * kThreads) {
+      const int64_t r = narrow ? (int64_t)((uint32_t)e / (uint32_t)ld) : e / ld;
+      const int64_t j = e - r * ld;
+      const float xr = __ldg(sg.x + r);
+      if (e + 4 <= e1 && j + 4 <= sg.n) {
+        const float4 y4 = __ldg(reinterpret_cast<const float4*>(sg.y + j));
+        float4 c = __ldcs(reinterpret_cast<const float4*>(sg.src + e));
+        c.x = __fmaf_rn(xr, __fmul_rn(sg.alpha, y4.x), c.x);
+        c.y = __fmaf_rn(xr, __fmul_rn(sg.alpha, y4.y), c.y);
+        c.z = __fmaf_rn(xr, __fmul_rn(sg.alpha, y4.z), c.z);
+        c.w = __fmaf_rn(xr, __fmul_rn(sg.alpha, y4.w), c.w);
+        *reinterpret_cast<float4*>(d + e) = c;
+      } else {
+        for (int q = 0; q < 4 && e + q < e1; ++q) {
+          const float c = sg.src[e + q];
+          d[e + q] = j + q < sg.n ? __fmaf_rn(xr, __fmul_rn(sg.alpha, __ldg(sg.y + j + q)), c) : c;
+        }
       }
     }
   }
@@ -183,12 +231,16 @@ struct Piece {
 struct Footprint {
   int64_t ld = 0;
   Piece p[3] = {};  // GEMV: A|Q, x, c; DOT: x, y, alpha; GER: C, x, y
+                    // (from the pool: the output alone, c, alpha or C)
   int pieces = 0;
   size_t total = 0;
+  int64_t extent[3] = {};  // elements of operand streams 1, 2, 3
 };
 
+inline bool pooled(const gb_request& r) { return (r.flags & GB_REQ_POOL) != 0; }
+
 inline bool request_ok(const gb_request& r) {
-  if (r.reserved != 0) return false;
+  if ((r.flags & ~GB_REQ_POOL) != 0) return false;
   if (r.n < 1 || r.n > INT32_MAX) return false;
   switch (r.op) {
     case GB_REQ_GEMV:
@@ -209,33 +261,51 @@ Footprint footprint(const gb_request& r) {
     f.total += round_up(bytes > 0 ? bytes : 1, kAlign);
   };
   const size_t m = (size_t)r.m, n = (size_t)r.n;
+  const bool pool = pooled(r);
   if (r.op == GB_REQ_GEMV) {
-    if (r.form == GB_FORM_BF16) {
-      f.ld = (int64_t)round_up(n, 8);
-      add(m * (size_t)f.ld * 2);
-    } else {
-      f.ld = (int64_t)round_up(n, 4);
-      add(m * (size_t)f.ld * 4);
+    f.ld = (int64_t)round_up(n, r.form == GB_FORM_BF16 ? 8 : 4);
+    f.extent[0] = (int64_t)(m * (size_t)f.ld);
+    f.extent[1] = (int64_t)n;
+    f.extent[2] = (int64_t)m;
+    if (!pool) {
+      add(m * (size_t)f.ld * (r.form == GB_FORM_BF16 ? 2 : 4));
+      add(n * 4);
     }
-    add(n * 4);
     add(m * 4);
   } else if (r.op == GB_REQ_DOT) {
     f.ld = (int64_t)round_up(n, 4);
-    add((size_t)f.ld * 4);  // x, stored as the one row of a GEMV
-    add(n * 4);
+    f.extent[0] = f.extent[1] = (int64_t)n;
+    f.extent[2] = 1;
+    if (!pool) {
+      add((size_t)f.ld * 4);  // x, stored as the one row of a GEMV
+      add(n * 4);
+    }
     add(4);
   } else {
     f.ld = (int64_t)round_up(n, 4);
+    f.extent[0] = (int64_t)(m * (size_t)f.ld);
+    f.extent[1] = (int64_t)m;
+    f.extent[2] = (int64_t)n;
     add(m * (size_t)f.ld * 4);
-    add(m * 4);
-    add(n * 4);
+    if (!pool) {
+      add(m * 4);
+      add(n * 4);
+    }
   }
   return f;
+}
+
+// Start (elements) of operand stream s in a pool of P elements:
+// 8 * (mix(key(seed, s)) mod (floor((P - L) / 8) + 1)), L <= P.
+inline int64_t pool_offset(uint64_t seed, uint64_t s, int64_t extent, int64_t P) {
+  const uint64_t slots = (uint64_t)((P - extent) / 8) + 1;
+  return (int64_t)(8 * (sm_mix(stream_key(seed, s)) % slots));
 }
 
 struct Req {
   gb_request r;
   Footprint f;
+  int64_t pool_off[3] = {};  // GB_REQ_POOL: element offsets of operand streams 1, 2, 3
   size_t off = 0;
   unsigned char* base = nullptr;  // device address of the range (host-only: nullptr)
   int64_t admit_ns = 0, launch_ns = 0, done_ns = 0, step = -1;
@@ -277,6 +347,9 @@ struct gb_engine {
   gb_batch_tuning table[GB_BATCH_BUCKETS];
   bool host_only = false;
   unsigned char* arena_base = nullptr;
+  float* pool_f32 = nullptr;      // resident operands (GB_REQ_POOL)
+  uint16_t* pool_bf16 = nullptr;
+  size_t pool_bytes = 0;
   Arena arena;
   std::vector<Slot> slots;
 
@@ -403,43 +476,82 @@ int gb_engine::ensure_capacity(Slot& s, size_t bytes) {
   return GB_OK;
 }
 
-// Enqueue one step: descriptors, operand fill, one batched launch for every
-// request, result copies, event.
+// Enqueue one step: descriptors, one operand kernel (operands drawn by the
+// generator; for pool requests the copies of the initial outputs and the
+// GERs), one batched launch for the GEMVs and DOTs (and the GERs of drawn
+// requests), result copies, event.
 int gb_engine::launch_step(Slot& s, std::vector<Req*>& reqs) {
-  // operand segments (inputs only; outputs of GER/GEMV/DOT are inputs too)
-  std::vector<FillSeg> segs;
+  std::vector<OperandSeg> segs;
+  auto fill = [&](void* dst, int64_t count, uint64_t key, int32_t kind) {
+    OperandSeg g{};
+    g.dst = dst;
+    g.count = count;
+    g.key = key;
+    g.kind = kind;
+    segs.push_back(g);
+  };
   for (Req* q : reqs) {
     const gb_request& r = q->r;
     const uint64_t seed = r.seed;
-    if (r.op == GB_REQ_GEMV) {
-      const int kind = r.form == GB_FORM_BF16 ? kFillBF16 : kFillF32;
-      segs.push_back({q->ptr(0), r.m * q->f.ld, stream_key(seed, 1), kind, 0});
-      segs.push_back({q->ptr(1), r.n, stream_key(seed, 2), kFillF32, 0});
-      segs.push_back({q->ptr(2), r.m, stream_key(seed, 3), kFillF32, 0});
+    if (pooled(r)) {
+      const float* P = pool_f32;
+      OperandSeg g{};
+      g.dst = q->ptr(0);
+      if (r.op == GB_REQ_GER) {
+        g.src = P + q->pool_off[0];
+        g.x = P + q->pool_off[1];
+        g.y = P + q->pool_off[2];
+        g.count = r.m * q->f.ld;
+        g.key = (uint64_t)q->f.ld;
+        g.kind = kGerF32;
+        g.n = (int32_t)r.n;
+        g.alpha = r.alpha;
+      } else {
+        g.src = P + q->pool_off[2];
+        g.count = r.op == GB_REQ_GEMV ? r.m : 1;
+        g.kind = kCopyF32;
+      }
+      segs.push_back(g);
+    } else if (r.op == GB_REQ_GEMV) {
+      fill(q->ptr(0), r.m * q->f.ld, stream_key(seed, 1), r.form == GB_FORM_BF16 ? kFillBF16 : kFillF32);
+      fill(q->ptr(1), r.n, stream_key(seed, 2), kFillF32);
+      fill(q->ptr(2), r.m, stream_key(seed, 3), kFillF32);
     } else if (r.op == GB_REQ_DOT) {
-      segs.push_back({q->ptr(0), r.n, stream_key(seed, 1), kFillF32, 0});
-      segs.push_back({q->ptr(1), r.n, stream_key(seed, 2), kFillF32, 0});
-      segs.push_back({q->ptr(2), 1, stream_key(seed, 3), kFillF32, 0});
+      fill(q->ptr(0), r.n, stream_key(seed, 1), kFillF32);
+      fill(q->ptr(1), r.n, stream_key(seed, 2), kFillF32);
+      fill(q->ptr(2), 1, stream_key(seed, 3), kFillF32);
     } else {
-      segs.push_back({q->ptr(0), r.m * q->f.ld, stream_key(seed, 1), kFillF32, 0});
-      segs.push_back({q->ptr(1), r.m, stream_key(seed, 2), kFillF32, 0});
-      segs.push_back({q->ptr(2), r.n, stream_key(seed, 3), kFillF32, 0});
+      fill(q->ptr(0), r.m * q->f.ld, stream_key(seed, 1), kFillF32);
+      fill(q->ptr(1), r.m, stream_key(seed, 2), kFillF32);
+      fill(q->ptr(2), r.n, stream_key(seed, 3), kFillF32);
     }
   }
   std::vector<int64_t> first(segs.size() + 1, 0);
   for (size_t i = 0; i < segs.size(); ++i)
     first[i + 1] = first[i] + (segs[i].count + kFillChunk - 1) / kFillChunk;
 
-  // every request's compute in one batched launch: GEMVs (FP32 or BF16 A),
-  // DOTs as one-row FP32 GEMVs, GERs
+  // every GEMV (FP32 or BF16 A) and DOT (a one-row FP32 GEMV) in one
+  // batched launch, with the GERs of drawn requests
   std::vector<BatchItem> items;
   items.reserve(reqs.size());
   for (Req* q : reqs) {
     const gb_request& r = q->r;
+    const bool pool = pooled(r);
+    if (pool && r.op == GB_REQ_GER) continue;  // done by the operand kernel
     BatchItem it{};
     it.n = r.n;
     it.lda = q->f.ld;
-    if (r.op == GB_REQ_GEMV) {
+    if (pool) {
+      const float* P = pool_f32;
+      it.kind = r.op == GB_REQ_GEMV && r.form == GB_FORM_BF16 ? kBatchGemvBF16 : kBatchGemvF32;
+      it.m = r.op == GB_REQ_GEMV ? r.m : 1;
+      it.alpha = r.op == GB_REQ_GEMV ? r.alpha : 1.0f;
+      // GEMV kinds only read A
+      it.A = it.kind == kBatchGemvBF16 ? static_cast<void*>(pool_bf16 + q->pool_off[0])
+                                       : static_cast<void*>(pool_f32 + q->pool_off[0]);
+      it.x = P + q->pool_off[1];
+      it.c = reinterpret_cast<float*>(q->ptr(0));
+    } else if (r.op == GB_REQ_GEMV) {
       it.kind = r.form == GB_FORM_BF16 ? kBatchGemvBF16 : kBatchGemvF32;
       it.m = r.m;
       it.alpha = r.alpha;
@@ -468,12 +580,12 @@ int gb_engine::launch_step(Slot& s, std::vector<Req*>& reqs) {
   if (plan_bytes == 0) return GB_ERR_UNSUPPORTED;
 
   // staging layout: segs | first | plan
-  const size_t o_first = round_up(segs.size() * sizeof(FillSeg), 16);
+  const size_t o_first = round_up(segs.size() * sizeof(OperandSeg), 16);
   const size_t o_plan = round_up(o_first + first.size() * sizeof(int64_t), 256);
   const size_t total = o_plan + plan_bytes;
   int st = ensure_capacity(s, total);
   if (st != GB_OK) return st;
-  std::memcpy(s.host, segs.data(), segs.size() * sizeof(FillSeg));
+  std::memcpy(s.host, segs.data(), segs.size() * sizeof(OperandSeg));
   std::memcpy(s.host + o_first, first.data(), first.size() * sizeof(int64_t));
   st = batch_plan(nb, items.data(), table, s.host + o_plan, plan_bytes);
   if (st != GB_OK) return GB_ERR_UNSUPPORTED;
@@ -481,21 +593,22 @@ int gb_engine::launch_step(Slot& s, std::vector<Req*>& reqs) {
   if (cudaMemcpyAsync(s.dev, s.host, total, cudaMemcpyHostToDevice, sm) != cudaSuccess) return GB_ERR_CUDA;
   if (!segs.empty()) {
     const int64_t blocks = first.back();
-    fill_kernel<<<(unsigned)blocks, kThreads, 0, sm>>>(reinterpret_cast<const FillSeg*>(s.dev),
-                                                       reinterpret_cast<const int64_t*>(s.dev + o_first),
-                                                       (int)segs.size());
+    operand_kernel<<<(unsigned)blocks, kThreads, 0, sm>>>(reinterpret_cast<const OperandSeg*>(s.dev),
+                                                          reinterpret_cast<const int64_t*>(s.dev + o_first),
+                                                          (int)segs.size());
     if (cudaPeekAtLastError() != cudaSuccess) return GB_ERR_CUDA;
   }
-  if (gb_sgemv_batch(s.host + o_plan, s.dev + o_plan, sm) != GB_OK) return GB_ERR_CUDA;
+  if (nb > 0 && gb_sgemv_batch(s.host + o_plan, s.dev + o_plan, sm) != GB_OK) return GB_ERR_CUDA;
   for (Req* q : reqs) {
     const gb_request& r = q->r;
     if (!r.out) continue;
     cudaError_t e;
+    const unsigned char* res = pooled(r) || r.op == GB_REQ_GER ? q->ptr(0) : q->ptr(2);
     if (r.op == GB_REQ_GER)
-      e = cudaMemcpy2DAsync(r.out, (size_t)r.n * 4, q->ptr(0), (size_t)q->f.ld * 4, (size_t)r.n * 4, (size_t)r.m,
+      e = cudaMemcpy2DAsync(r.out, (size_t)r.n * 4, res, (size_t)q->f.ld * 4, (size_t)r.n * 4, (size_t)r.m,
                             cudaMemcpyDeviceToHost, sm);
     else
-      e = cudaMemcpyAsync(r.out, q->ptr(2), r.op == GB_REQ_DOT ? 4 : (size_t)r.m * 4, cudaMemcpyDeviceToHost, sm);
+      e = cudaMemcpyAsync(r.out, res, r.op == GB_REQ_DOT ? 4 : (size_t)r.m * 4, cudaMemcpyDeviceToHost, sm);
     if (e != cudaSuccess) return GB_ERR_CUDA;
   }
   if (cudaEventRecord(s.done, sm) != cudaSuccess) return GB_ERR_CUDA;
@@ -573,6 +686,45 @@ void gb_engine::run() {
   }
 }
 
+namespace {
+
+// Allocate the operand pools and draw them (FP32: stream 1 of the pool seed;
+// BF16: stream 2, rounded) on the first slot's stream; returns when done.
+int fill_pool(gb_engine* e) {
+  const int64_t P = e->cfg.pool_elems;
+  if (cudaMalloc(&e->pool_f32, (size_t)P * 4) != cudaSuccess) return GB_ERR_CUDA;
+  if (cudaMalloc(&e->pool_bf16, (size_t)P * 2) != cudaSuccess) return GB_ERR_CUDA;
+  e->pool_bytes = (size_t)P * 6;
+  OperandSeg segs[2] = {};
+  segs[0].dst = e->pool_f32;
+  segs[0].count = P;
+  segs[0].key = stream_key(e->cfg.pool_seed, 1);
+  segs[0].kind = kFillF32;
+  segs[1].dst = e->pool_bf16;
+  segs[1].count = P;
+  segs[1].key = stream_key(e->cfg.pool_seed, 2);
+  segs[1].kind = kFillBF16;
+  const int64_t per = (P + kFillChunk - 1) / kFillChunk;
+  const int64_t first[3] = {0, per, 2 * per};
+  unsigned char* d = nullptr;
+  if (cudaMalloc(&d, 256) != cudaSuccess) return GB_ERR_CUDA;
+  cudaStream_t sm = e->slots[0].stream;
+  int st = GB_OK;
+  if (cudaMemcpyAsync(d, segs, sizeof(segs), cudaMemcpyHostToDevice, sm) != cudaSuccess ||
+      cudaMemcpyAsync(d + 128, first, sizeof(first), cudaMemcpyHostToDevice, sm) != cudaSuccess) {
+    st = GB_ERR_CUDA;
+  } else {
+    operand_kernel<<<(unsigned)(2 * per), kThreads, 0, sm>>>(reinterpret_cast<const OperandSeg*>(d),
+                                                            reinterpret_cast<const int64_t*>(d + 128), 2);
+    if (cudaPeekAtLastError() != cudaSuccess) st = GB_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(sm) != cudaSuccess) st = GB_ERR_CUDA;
+  cudaFree(d);
+  return st;
+}
+
+}  // namespace
+
 extern "C" {
 
 int64_t gb_engine_now_ns(void) { return now_ns(); }
@@ -587,7 +739,8 @@ int gb_engine_create(const gb_engine_config* cfg, gb_engine** out) {
   if (!out) return -2;
   *out = nullptr;
   if (cfg->budget_bytes < ((size_t)1 << 20) || cfg->streams < 1 || cfg->streams > 16 ||
-      cfg->max_inflight < 1 || cfg->max_step_requests < 1 || (cfg->flags & ~GB_ENGINE_HOST_ONLY) != 0)
+      cfg->max_inflight < 1 || cfg->max_step_requests < 1 || (cfg->flags & ~GB_ENGINE_HOST_ONLY) != 0 ||
+      cfg->pool_elems < 0 || cfg->pool_elems % 8 != 0 || cfg->pool_elems > ((int64_t)1 << 40))
     return -1;
   const bool host_only = (cfg->flags & GB_ENGINE_HOST_ONLY) != 0;
   if (host_only && !(cfg->sim_bytes_per_ns > 0.0)) return -1;
@@ -614,6 +767,7 @@ int gb_engine_create(const gb_engine_config* cfg, gb_engine** out) {
       ok = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess &&
            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) == cudaSuccess;
     }
+    if (ok && cfg->pool_elems > 0) ok = fill_pool(e) == GB_OK;
     if (!ok) {
       cudaGetLastError();
       for (Slot& s : e->slots) {
@@ -621,6 +775,8 @@ int gb_engine_create(const gb_engine_config* cfg, gb_engine** out) {
         if (s.stream) cudaStreamDestroy(s.stream);
       }
       if (e->arena_base) cudaFree(e->arena_base);
+      if (e->pool_f32) cudaFree(e->pool_f32);
+      if (e->pool_bf16) cudaFree(e->pool_bf16);
       delete e;
       return GB_ERR_CUDA;
     }
@@ -638,6 +794,8 @@ int gb_engine_create(const gb_engine_config* cfg, gb_engine** out) {
       if (s.stream) cudaStreamDestroy(s.stream);
     }
     if (e->arena_base) cudaFree(e->arena_base);
+    if (e->pool_f32) cudaFree(e->pool_f32);
+    if (e->pool_bf16) cudaFree(e->pool_bf16);
     delete e;
     return GB_ERR_CUDA;
   }
@@ -658,6 +816,16 @@ int gb_engine_submit(gb_engine* e, const gb_request* r) {
   Req* q = new Req();
   q->r = *r;
   q->f = footprint(*r);
+  if (pooled(*r)) {
+    const int64_t P = e->cfg.pool_elems;
+    for (int k = 0; k < 3; ++k) {
+      if (q->f.extent[k] > P) {
+        delete q;
+        return -2;
+      }
+      q->pool_off[k] = pool_offset(r->seed, (uint64_t)(k + 1), q->f.extent[k], P);
+    }
+  }
   if (q->f.total > e->cfg.budget_bytes) {
     delete q;
     return GB_ERR_BUDGET;
@@ -706,6 +874,7 @@ int gb_engine_stats_get(gb_engine* e, gb_engine_stats* out) {
   out->bytes_in_use = e->bytes_in_use.load();
   out->bytes_peak = e->bytes_peak.load();
   out->budget_bytes = e->cfg.budget_bytes;
+  out->pool_bytes = e->pool_bytes;
   return 0;
 }
 
@@ -729,6 +898,8 @@ void gb_engine_destroy(gb_engine* e) {
   }
   for (Req* q : e->admitted) delete q;
   if (e->arena_base) cudaFree(e->arena_base);
+  if (e->pool_f32) cudaFree(e->pool_f32);
+  if (e->pool_bf16) cudaFree(e->pool_bf16);
   delete e;
 }
 

@@ -105,6 +105,15 @@ def uniform_pairs(n: int, seed: int, stream: int, offset: int = 0) -> np.ndarray
     return (b.astype(np.float32) * np.float32(2.0 ** -23) - np.float32(1.0)).astype(np.float32)
 
 
+def pool_offset(seed: int, stream: int, extent: int, pool_elems: int) -> int:
+    """Start (elements) of a serving request's operand in a resident pool of
+    pool_elems elements: 8 * (mix(key(seed, stream)) mod (floor((pool_elems
+    - extent) / 8) + 1)), extent <= pool_elems."""
+    with np.errstate(over="ignore"):
+        h = int(_mix(np.array([key(seed, stream)], np.uint64))[0])
+    return 8 * (h % ((pool_elems - extent) // 8 + 1))
+
+
 def log_uniform_integers(n: int, seed: int, stream: int, lo: int, hi: int) -> np.ndarray:
     """round(exp(ln lo + u (ln hi - ln lo))) with u uniform in [0, 1): sizes
     spread evenly over the decades between lo and hi (int64)."""

@@ -166,3 +166,46 @@ def test_engine_header_symbols_exported():
     assert names == sorted(gb.ENGINE_EXPORTS)
     for name in names:
         assert hasattr(gb.lib(), name)
+
+
+def test_pool_requests_hold_only_their_output():
+    """With resident operands (GB_REQ_POOL) a request holds its output alone
+    in the arena; operands longer than the pool, pool requests without a pool
+    and unknown flags are refused; pool sizes must be multiples of 8."""
+    assert gb.request_bytes(gb.REQ_GEMV, 10, 10, pool=True) == 256
+    assert gb.request_bytes(gb.REQ_GEMV, 1000, 1000, gb.FORM_BF16, pool=True) == 4096
+    assert gb.request_bytes(gb.REQ_DOT, 1, 1000, pool=True) == 256
+    assert gb.request_bytes(gb.REQ_GER, 1000, 1001, pool=True) == 1000 * 1004 * 4 // 256 * 256 + 256
+    P = 1 << 20
+    with gb.Engine(64 * MB, host_only=True, pool_elems=P, sim_bytes_per_ns=100.0) as e:
+        assert e.submit(0, gb.REQ_GEMV, 1024, 1024, pool=True) == gb.GB_OK        # A = 2^20 elements
+        assert e.submit(1, gb.REQ_GEMV, 1024, 1025, pool=True) == -2              # ld 1028: too long
+        assert e.submit(2, gb.REQ_GEMV, 1024, 1024, form=gb.FORM_BF16, pool=True) == gb.GB_OK
+        assert e.submit(3, gb.REQ_DOT, 1, P, pool=True) == gb.GB_OK
+        assert e.submit(4, gb.REQ_DOT, 1, P + 1, pool=True) == -2
+        assert e.submit(5, gb.REQ_GER, 2048, 512, pool=True) == gb.GB_OK
+        assert e.submit(6, gb.REQ_GER, 2048, 513, pool=True) == -2
+        r = gb.Request(7, gb.REQ_GEMV, 0, 8, 8, 1.0, 2, 0, None, 0)               # unknown flag
+        assert gb.gb_engine_submit(e.h, gb.ctypes.addressof(r)) == -2
+        assert e.drain(10000) == gb.GB_OK
+        done = sorted(e.poll(), key=lambda c: c["id"])
+        assert [c["id"] for c in done] == [0, 2, 3, 5]
+        assert [c["bytes"] for c in done] == [4096, 4096, 256, 2048 * 512 * 4]
+        assert e.stats()["pool_bytes"] == 0                                       # host-only: none allocated
+    with gb.Engine(64 * MB, host_only=True) as e:
+        assert e.submit(0, gb.REQ_GEMV, 8, 8, pool=True) == -2
+    h = gb.ctypes.c_void_p()
+    for bad in (-8, 12):
+        cfg = gb.EngineConfig(1 << 30, 1, 1, 1, gb.ENGINE_HOST_ONLY, 1.0, None, bad, 0)
+        assert gb.gb_engine_create(cfg, gb.ctypes.addressof(h)) == -1
+
+
+def test_pool_offsets_stay_inside_the_pool_and_are_aligned():
+    import synth
+    P = 1 << 16
+    for seed in range(200):
+        for s, L in ((1, 1), (2, 4093), (3, P), (1, P - 8), (2, 777)):
+            o = synth.pool_offset(seed, s, L, P)
+            assert o % 8 == 0 and 0 <= o and o + L <= P
+    offs = {synth.pool_offset(seed, 1, 1000, P) for seed in range(200)}
+    assert len(offs) > 150, "operands of different requests start at different places"

@@ -172,3 +172,115 @@ def test_full_size_stream_sampled():
     assert len(outs) >= 7
     for i, out in outs.items():
         check(reqs[i], out.numpy())
+
+
+# ------------------------------------------------- resident operand pool --
+
+POOL = 1 << 22
+POOL_SEED = 99
+
+
+def pool_operands(op, form, m, n, seed, P=POOL, pool_seed=POOL_SEED):
+    """The operands a GB_REQ_POOL request reads: windows of the FP32 pool
+    (stream 1 of the pool seed) or, for the A of a BF16 GEMV, of the BF16
+    pool (stream 2, rounded), at synth.pool_offset of each operand stream."""
+    def window(s, L, bf16=False):
+        o = synth.pool_offset(seed, s, L, P)
+        v = synth.uniform_pairs(L, pool_seed, 2 if bf16 else 1, offset=o)
+        return oracle.bf16_decode(oracle.bf16_encode(v)) if bf16 else v
+    if op == gb.REQ_GEMV:
+        ld = round_up(n, 8 if form == gb.FORM_BF16 else 4)
+        A = window(1, m * ld, form == gb.FORM_BF16).reshape(m, ld)[:, :n]
+        return np.ascontiguousarray(A), window(2, n), window(3, m)
+    if op == gb.REQ_DOT:
+        return window(1, n), window(2, n), window(3, 1)
+    ld = round_up(n, 4)
+    C = np.ascontiguousarray(window(1, m * ld).reshape(m, ld)[:, :n])
+    return C, window(2, m), window(3, n)
+
+
+def check_pool(req, got):
+    op, form, m, n, alpha, seed = req
+    if op == gb.REQ_GEMV:
+        A, x, c0 = pool_operands(op, form, m, n, seed)
+        want = oracle.gemv(0, m, n, alpha, A.ravel(), n, x, c0)
+        scale = oracle.gemv_scale(0, m, n, alpha, A.ravel(), n, x, c0)
+        assert rel_err(got, want, scale) <= 1e-5, req
+    elif op == gb.REQ_DOT:
+        x, y, a0 = pool_operands(op, form, m, n, seed)
+        want = oracle.dot(n, x, y, float(a0[0]))
+        assert abs(float(got[0]) - want) <= 1e-5 * oracle.dot_scale(n, x, y, float(a0[0])), req
+    else:
+        C, x, y = pool_operands(op, form, m, n, seed)
+        want = oracle.ger(0, m, n, alpha, x, y, C.ravel(), n)
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), req
+
+
+def serve_pool(reqs, offsets, budget=1 << 30, streams=4, max_step=256):
+    outs = []
+    with gb.Engine(budget, streams=streams, max_inflight=4096, max_step_requests=max_step,
+                   pool_elems=POOL, pool_seed=POOL_SEED) as e:
+        assert e.stats()["pool_bytes"] == POOL * 6
+        t0 = e.now_ns() + 50_000_000
+        for i, (op, form, m, n, alpha, seed) in enumerate(reqs):
+            out = torch.empty(out_elems(op, m, n), dtype=torch.float32, pin_memory=True)
+            outs.append(out)
+            assert e.submit(i, op, m, n, alpha, seed, out, arrival_ns=int(t0 + offsets[i]), form=form,
+                            pool=True) == gb.GB_OK
+        assert e.drain(120000) == gb.GB_OK
+        done = e.poll()
+        stats = e.stats()
+    assert len(done) == len(reqs) and all(c["status"] == gb.GB_OK for c in done)
+    return [o.numpy().copy() for o in outs], done, stats
+
+
+def test_pool_mix_against_oracle():
+    reqs, t = stream(120, 4)
+    outs, done, stats = serve_pool(reqs, t)
+    assert stats["steps"] >= 2
+    for r, o in zip(reqs, outs):
+        check_pool(r, o)
+
+
+def test_pool_alone_equals_mix_bit_exact():
+    reqs, t = stream(60, 5, rate=200000.0)
+    mixed, done, _ = serve_pool(reqs, t)
+    assert max(np.bincount([c["step"] for c in done])) > 1, "the mix shares steps"
+    for i in (0, 5, 11, 23, 42, 59):
+        alone, _, _ = serve_pool([reqs[i]], [0], streams=1)
+        assert np.array_equal(alone[0].view(np.uint32), mixed[i].view(np.uint32)), reqs[i]
+
+
+def test_pool_contents_are_the_documented_generator():
+    """GER with alpha 0 returns C0: the FP32 pool window at its documented
+    offset, bit for bit (the BF16 pool is checked by the BF16 GEMVs against
+    the oracle)."""
+    reqs = [(gb.REQ_GER, gb.FORM_F32, m, n, 0.0, 300 + k) for k, (m, n) in
+            enumerate(((1, 1), (3, 5), (7, 13), (33, 1023), (1024, 4096)))]
+    outs, _, _ = serve_pool(reqs, [0] * len(reqs))
+    for (op, form, m, n, alpha, seed), got in zip(reqs, outs):
+        C, _, _ = pool_operands(op, form, m, n, seed)
+        assert np.array_equal(got.reshape(m, n).view(np.uint32), C.view(np.uint32)), (m, n)
+
+
+def test_pool_bf16_and_edges():
+    """BF16 GEMVs, DOTs and GERs of ragged sizes, and operands as long as the
+    pool allows (offset 0 is then the only start)."""
+    side = 2048                               # 2048 x 2048 = POOL
+    reqs = [(gb.REQ_GEMV, gb.FORM_BF16, m, n, 0.5, 400 + k) for k, (m, n) in
+            enumerate(((1, 1), (5, 7), (64, 129), (333, 1000), (side, side)))]
+    reqs += [(gb.REQ_DOT, gb.FORM_F32, 1, n, 1.0, 500 + k) for k, n in enumerate((1, 3, 4097, POOL))]
+    reqs += [(gb.REQ_GER, gb.FORM_F32, m, n, -1.5, 600 + k) for k, (m, n) in
+             enumerate(((1, 1), (9, 3), (100, 1001), (side, side)))]
+    outs, _, _ = serve_pool(reqs, [0] * len(reqs))
+    for r, o in zip(reqs, outs):
+        check_pool(r, o)
+
+
+def test_pool_refusals():
+    with gb.Engine(1 << 30, pool_elems=POOL) as e:
+        assert e.submit(0, gb.REQ_GER, 2048, 2049, pool=True) == -2       # ld 2052 x 2048 > POOL
+        assert e.submit(1, gb.REQ_DOT, 1, POOL + 1, pool=True) == -2
+        assert e.stats()["submitted"] == 0
+    with gb.Engine(1 << 30) as e:
+        assert e.submit(0, gb.REQ_GEMV, 8, 8, pool=True) == -2            # no pool
