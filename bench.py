@@ -990,7 +990,7 @@ def main(argv=None):
     p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--e2e-steps", type=int, default=5, help="steps of the host-buffer (e2e) leg")
+    p.add_argument("--e2e-steps", type=int, default=16, help="steps of the host-buffer (e2e) leg")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     p.add_argument("--no-growth", action="store_true",
