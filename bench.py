@@ -286,11 +286,13 @@ def gen_streams():
     return st
 
 
-def oracle_sample(fraction: int, seed: int = 0):
+def oracle_sample(fraction: int, seed: int = 0, acc: bool = False):
     """A bounded sample of one step for the CPU oracle: 1/fraction of the
     rows of each row-major GEMV/GER (at least one), of the columns of each
     column-major one, and of the DOT vectors, with the same generator values
-    the GPU step uses.  Returns [(callable, algorithmic bytes)]."""
+    the GPU step uses; GEMV and DOT by the plain definitions, or by the
+    compensated (Dot2) oracle with acc.  Returns [(callable, algorithmic
+    bytes)]."""
     import numpy as np
     import oracle
     import synth
@@ -305,20 +307,20 @@ def oracle_sample(fraction: int, seed: int = 0):
                 A = synth.uniform(k * n, seed, st[("A", sh, dt)], npdt)
                 x = synth.uniform(n, seed, st[("x", sh, dt)], npdt)
                 c = synth.uniform(k, seed, st[("c", sh, dt)], npdt)
-                work.append((lambda A=A, x=x, c=c, k=k, n=n: oracle.gemv(0, k, n, 1.0, A, n, x, c, acc=False),
+                work.append((lambda A=A, x=x, c=c, k=k, n=n: oracle.gemv(0, k, n, 1.0, A, n, x, c, acc=acc),
                              alg_bytes("gemv", dt, k, n)))
             else:
                 k = max(1, n // fraction)
                 A = synth.uniform(m * k, seed, st[("A", sh, dt)], npdt)
                 x = synth.uniform(k, seed, st[("x", sh, dt)], npdt)
                 c = synth.uniform(m, seed, st[("c", sh, dt)], npdt)
-                work.append((lambda A=A, x=x, c=c, k=k, m=m: oracle.gemv(1, m, k, 1.0, A, m, x, c, acc=False),
+                work.append((lambda A=A, x=x, c=c, k=k, m=m: oracle.gemv(1, m, k, 1.0, A, m, x, c, acc=acc),
                              alg_bytes("gemv", dt, m, k)))
         elif kind == "dot":
             k = max(1, n // fraction)
             x = synth.uniform(k, seed, st[("dx", dt)], npdt)
             y = synth.uniform(k, seed, st[("dy", dt)], npdt)
-            work.append((lambda x=x, y=y, k=k: oracle.dot(k, x, y, 0.0, acc=False),
+            work.append((lambda x=x, y=y, k=k: oracle.dot(k, x, y, 0.0, acc=acc),
                          alg_bytes("dot", dt, 1, k)))
         else:
             tag = "row" if lay == 0 else "col"
@@ -856,8 +858,24 @@ def run_ours(args):
         while secs < 10.0:          # repeat the sample until ~10 s of oracle time
             t, b = time_sample(work)
             secs, sb = secs + t, sb + b
+        extra = {}
+        for name, frac, threads, acc in (("single_thread", CPU_FRACTION * 16, 1, False),
+                                         ("acc", CPU_FRACTION * 4, oracle.threads(), True)):
+            w2 = oracle_sample(frac, acc=acc)
+            keep = oracle.threads()
+            oracle.set_threads(threads)
+            try:
+                t2, b2 = 0.0, 0
+                while t2 < 3.0:
+                    t, b = time_sample(w2)
+                    t2, b2 = t2 + t, b2 + b
+            finally:
+                oracle.set_threads(keep)
+            extra[name] = {"value": round(b2 / t2 / 1e9, 3), "cores": threads,
+                           "sample": f"1/{frac} of a step, {b2 / 1e9:.2f} GB in {t2:.1f} s"}
         cpu = {"value": round(sb / secs / 1e9, 3), "unit": "GB/s", "cores": oracle.threads(),
-               "kind": "oracle",
+               "kind": "oracle", "single_thread": extra["single_thread"],
+               "acc_oracle": extra["acc"],
                "sample": f"1/{CPU_FRACTION} of the rows (row-major) or columns (column-major) of "
                          f"every GEMV/GER and of the DOT vectors of one step (DOT single-threaded), "
                          f"plain FP64 oracle, repeated: {sb / 1e9:.2f} GB in {secs:.1f} s; "
