@@ -634,7 +634,7 @@ def serve_stream(count, rate, seed, lo=32, hi=16384):
     return t, ops, m, n
 
 
-def serve_once(count, rate, form, seed=0, sample=8, pool=True):
+def serve_once(count, rate, form, seed=0, sample=8, pool=True, budget=SERVE_BUDGET, pool_elems=SERVE_POOL):
     """Serve one stream (operands from the resident pools, or drawn per
     request); returns throughput, latency percentiles and the measured error
     of `sample` GEMV results (numpy FP64 on the generator's FP32 values,
@@ -647,8 +647,8 @@ def serve_once(count, rate, form, seed=0, sample=8, pool=True):
     gemv_idx = [i for i in range(count) if ops[i] == 0 and m[i] * n[i] <= 1 << 22]
     picks = set(gemv_idx[::max(1, len(gemv_idx) // sample)][:sample]) if sample > 0 else set()
     outs = {}
-    with gb.Engine(SERVE_BUDGET, streams=4, max_inflight=16384, max_step_requests=512,
-                   table=gb.load_tuning(), pool_elems=SERVE_POOL if pool else 0,
+    with gb.Engine(budget, streams=4, max_inflight=16384, max_step_requests=512,
+                   table=gb.load_tuning(), pool_elems=pool_elems if pool else 0,
                    pool_seed=SERVE_POOL_SEED) as e:
         t0 = e.now_ns() + int(0.2e9) + count * 20000   # every request is queued before the first arrives
         for i in range(count):
@@ -680,7 +680,7 @@ def serve_once(count, rate, form, seed=0, sample=8, pool=True):
         s0 = seed * 1000003 + i
         if pool:    # windows of the pools; the BF16 pool rounds stream 2 of the pool seed
             def win(s, L, stream):
-                o = synth.pool_offset(s0, s, L, SERVE_POOL)
+                o = synth.pool_offset(s0, s, L, pool_elems)
                 return synth.uniform_pairs(L, SERVE_POOL_SEED, stream, offset=o)
             A = win(1, mi * ld, 2 if form == gb.FORM_BF16 else 1)
             x, c0 = win(2, ni, 1), win(3, mi, 1)

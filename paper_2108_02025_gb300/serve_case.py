@@ -1,11 +1,15 @@
 """Serve one seeded Poisson stream through the engine and print its summary.
 
     python -m paper_2108_02025_gb300.serve_case [--requests 2000] [--rate 1e7] [--bf16]
+        [--drawn] [--budget-gb 64] [--pool-log2 30]
 
 The stream is the serving workload (70% GEMV / 20% DOT / 10% GER, m and n
-log-uniform in [32, 16384], 64 GB budget, 4 streams); with the default rate
-every request arrives at once, which measures capacity.  Used to profile
-the engine's kernels in isolation.
+log-uniform in [32, 16384], 4 streams), on resident operand pools of
+2^pool-log2 FP32 and BF16 values (or with every operand drawn per request,
+--drawn) under an HBM budget of --budget-gb GB; with the default rate every
+request arrives at once, which measures capacity.  Used to profile the
+engine's kernels in isolation (a small budget and pool keep the device
+footprint of a profiler capture small).
 """
 from __future__ import annotations
 
@@ -25,11 +29,15 @@ def main(argv=None):
     p.add_argument("--rate", type=float, default=1e7)
     p.add_argument("--bf16", action="store_true")
     p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--drawn", action="store_true", help="operands drawn per request, no pool")
+    p.add_argument("--budget-gb", type=float, default=64.0)
+    p.add_argument("--pool-log2", type=int, default=30)
     args = p.parse_args(argv)
     import bench
     import paper_2108_02025_gb300 as gb
     r = bench.serve_once(args.requests, args.rate, gb.FORM_BF16 if args.bf16 else gb.FORM_F32, seed=args.seed,
-                         sample=0)
+                         sample=0, pool=not args.drawn, budget=int(args.budget_gb * (1 << 30)),
+                         pool_elems=1 << args.pool_log2)
     print(json.dumps(r))
 
 
