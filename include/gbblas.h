@@ -117,6 +117,17 @@ size_t gb_workspace_bytes(int op, int dtype, int layout, int64_t m, int64_t n);
    GB_ERR_CUDA. */
 int gb_workspace_init(void *ws, size_t ws_bytes, gb_stream stream);
 
+/* Copy `bytes` bytes from device memory `src` to page-locked host memory
+   `dst` (cudaHostAlloc, cudaHostRegister or a pinned tensor) with a kernel
+   on `stream` that stores through the host buffer's device mapping, so the
+   copy uses no copy engine and overlaps copy-engine transfers in the other
+   direction.  Any alignment (16-byte aligned pointers take the wide path).
+   Returns GB_OK (also for bytes == 0), -1 if dst is NULL or not page-locked
+   host memory, -2 if src is NULL or overlaps dst, GB_ERR_CUDA if the launch
+   failed.  Not an operation of the paper: IO for callers whose results go
+   back to host memory. */
+int gb_copy_to_host(void *dst, const void *src, size_t bytes, gb_stream stream);
+
 /* GEMV, Def. GEMV (Sec. 3.1), Alg. 1 (column-major) and Alg. 2 (row-major):
    c_i <- c_i + alpha * sum_j A_ij x_j for i < m.
      layout  GB_ROW_MAJOR or GB_COL_MAJOR                         (arg 1)

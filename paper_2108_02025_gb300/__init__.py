@@ -50,6 +50,7 @@ def _load() -> ctypes.CDLL:
     lib.gb_status_string.argtypes, lib.gb_status_string.restype = [I], ctypes.c_char_p
     lib.gb_workspace_bytes.argtypes, lib.gb_workspace_bytes.restype = [I, I, I, I64, I64], SZ
     lib.gb_workspace_init.argtypes, lib.gb_workspace_init.restype = [P, SZ, P], I
+    lib.gb_copy_to_host.argtypes, lib.gb_copy_to_host.restype = [P, P, SZ, P], I
     lib.gb_dgemv.argtypes = [I, I64, I64, D, P, I64, P, P, P, SZ, P]
     lib.gb_sgemv.argtypes = [I, I64, I64, F, P, I64, P, P, P, SZ, P]
     lib.gb_ddot.argtypes = [I64, P, P, P, P, SZ, P]
@@ -89,7 +90,7 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 
 # Every symbol the header declares (checked by the tests against include/gbblas.h).
-EXPORTS = ("gb_version", "gb_status_string", "gb_workspace_bytes", "gb_workspace_init",
+EXPORTS = ("gb_version", "gb_status_string", "gb_workspace_bytes", "gb_workspace_init", "gb_copy_to_host",
            "gb_dgemv", "gb_sgemv", "gb_ddot", "gb_sdot", "gb_dger", "gb_sger",
            "gb_dgemv_noalloc", "gb_quantize_bf16", "gb_quantize_e4m3", "gb_gemv_bf16",
            "gb_gemv_e4m3", "gb_sgemv_batch_default_tuning", "gb_sgemv_batch_plan_bytes",
@@ -143,6 +144,10 @@ def gb_workspace_bytes(op: int, dtype: int, layout: int, m: int, n: int) -> int:
 
 def gb_workspace_init(ws, ws_bytes: int, stream=None) -> int:
     return _lib.gb_workspace_init(_ptr(ws), ws_bytes, _stream(stream))
+
+
+def gb_copy_to_host(dst, src, nbytes: int, stream=None) -> int:
+    return _lib.gb_copy_to_host(_ptr(dst), _ptr(src), nbytes, _stream(stream))
 
 
 def gb_dgemv(layout, m, n, alpha, A, lda, x, c, ws, ws_bytes, stream=None) -> int:

@@ -29,7 +29,7 @@ def declared():
 
 def test_every_declared_symbol_is_exported():
     names = declared()
-    assert len(names) == 22
+    assert len(names) == 23
     for name in names:
         assert hasattr(gb.lib(), name), name
     assert sorted(gb.EXPORTS) == names
