@@ -614,11 +614,13 @@ def run_batched(device, stream, hbm, reps=5):
 SERVE_WORKLOAD = ("Poisson request stream, 70% GEMV / 20% DOT / 10% GER, m and n log-uniform in "
                   "[32, 16384], alpha 1, operands resident on the device (pools of 2^30 FP32 and "
                   "2^30 BF16 values from the counter-based generator, filled once), each request's "
-                  "output allocated under a 64 GB HBM admission budget, 4 streams; for comparison "
-                  "the same stream with every operand drawn on the device per request")
+                  "output allocated under a 64 GB HBM admission budget, 4 streams, GEMVs and GERs "
+                  "above 256 MB launched in row chunks of about 256 MB; for comparison the same "
+                  "stream with every operand drawn on the device per request")
 SERVE_BUDGET = 64 << 30
 SERVE_POOL = 1 << 30
 SERVE_POOL_SEED = 2108
+SERVE_CHUNK = 256 << 20   # pool GEMVs / GERs above this many bytes run in row chunks of about this size
 
 
 def serve_stream(count, rate, seed, lo=32, hi=16384):
@@ -634,7 +636,8 @@ def serve_stream(count, rate, seed, lo=32, hi=16384):
     return t, ops, m, n
 
 
-def serve_once(count, rate, form, seed=0, sample=8, pool=True, budget=SERVE_BUDGET, pool_elems=SERVE_POOL):
+def serve_once(count, rate, form, seed=0, sample=8, pool=True, budget=SERVE_BUDGET, pool_elems=SERVE_POOL,
+               chunk_bytes=SERVE_CHUNK):
     """Serve one stream (operands from the resident pools, or drawn per
     request); returns throughput, latency percentiles and the measured error
     of `sample` GEMV results (numpy FP64 on the generator's FP32 values,
@@ -649,7 +652,7 @@ def serve_once(count, rate, form, seed=0, sample=8, pool=True, budget=SERVE_BUDG
     outs = {}
     with gb.Engine(budget, streams=4, max_inflight=16384, max_step_requests=512,
                    table=gb.load_tuning(), pool_elems=pool_elems if pool else 0,
-                   pool_seed=SERVE_POOL_SEED) as e:
+                   pool_seed=SERVE_POOL_SEED, chunk_bytes=chunk_bytes) as e:
         t0 = e.now_ns() + int(0.2e9) + count * 20000   # every request is queued before the first arrives
         for i in range(count):
             out = None
@@ -707,21 +710,29 @@ def serve_once(count, rate, form, seed=0, sample=8, pool=True, budget=SERVE_BUDG
 SERVE_LOADS = (0.5, 0.8, 0.95)
 
 
+def serve_loads(count, form, seed=1, chunk_bytes=SERVE_CHUNK, pool=True):
+    """One stream at saturation, then the same requests (same sizes, same
+    order) arriving at 50%, 80% and 95% of the measured rate."""
+    sat = serve_once(count, 1e7, form, seed=seed, chunk_bytes=chunk_bytes, pool=pool)
+    loads = {str(f): serve_once(count, sat["solves_per_s"] * f, form, seed=seed, chunk_bytes=chunk_bytes, pool=pool)
+             for f in SERVE_LOADS}
+    return {"saturated": sat, "loads": loads}
+
+
 def run_serving(count=20000):
-    """Saturating streams (throughput) for FP32 and BF16-stored A, then each
-    at 50%, 80% and 95% of its measured throughput (latency under load)."""
+    """Saturating streams (throughput) for FP32 and BF16-stored A, then the
+    same streams at 50%, 80% and 95% of their measured throughput (latency
+    under load)."""
     import paper_2108_02025_gb300 as gb
     out = {"workload": SERVE_WORKLOAD, "budget_bytes": SERVE_BUDGET,
            "error_bound": {"fp32": "1e-5 of sum|A x| + |c0| (FP32 accumulation)",
                            "bf16": "2^-9 of sum|A x| + |c0| (BF16 rounding of A) + FP32 accumulation"}}
+    out["chunk_bytes"] = SERVE_CHUNK
     for name, form in (("fp32", gb.FORM_F32), ("bf16", gb.FORM_BF16)):
-        sat = serve_once(count, 1e7, form, seed=1)
-        loads = {str(f): serve_once(count // 2, sat["solves_per_s"] * f, form, seed=2 + k)
-                 for k, f in enumerate(SERVE_LOADS)}
-        out[name] = {"saturated": sat, "loads": loads}
+        out[name] = serve_loads(count, form)
     out["bf16_speedup_solves"] = round(out["bf16"]["saturated"]["solves_per_s"] /
                                        out["fp32"]["saturated"]["solves_per_s"], 3)
-    out["drawn_operands"] = {name: serve_once(count, 1e7, form, seed=1, pool=False)
+    out["drawn_operands"] = {name: serve_once(count, 1e7, form, seed=1, pool=False, chunk_bytes=0)
                              for name, form in (("fp32", gb.FORM_F32), ("bf16", gb.FORM_BF16))}
     return out
 

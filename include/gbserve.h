@@ -57,6 +57,17 @@
  * the pools are never written.  A request whose operand is longer than P is
  * refused (-2).
  *
+ * Chunks (chunk_bytes > 0).  A step takes the admitted requests that are
+ * launched whole first, in admission order, then rows of the chunked
+ * requests (GB_REQ_POOL GEMVs and GERs whose rows move more than
+ * chunk_bytes: the A row and c element, or the C0 and C rows) in admission
+ * order, at least one row and at most about chunk_bytes of them per step.
+ * A large request then holds the GPU a chunk at a time, so smaller requests
+ * that arrive meanwhile run between its chunks.  Rows are independent
+ * (each row's sum, or each element, is computed as it would be whole), so
+ * the results do not change; the request completes when its last chunk and
+ * every earlier one are done.
+ *
  * Results.  `out`, when not NULL, must be page-locked host memory (for
  * example from cudaHostAlloc or a pinned tensor): GEMV writes m floats (c),
  * DOT one float (alpha), GER m * n floats (C, row-major, packed).  The copy
@@ -109,6 +120,9 @@ typedef struct {
   int64_t pool_elems;           /* resident operand pool: elements (0 = none, else a
                                    multiple of 8, at most 2^40) */
   uint64_t pool_seed;           /* generator seed of the pool */
+  size_t chunk_bytes;           /* 0, or: pool GEMVs and GERs moving more than this
+                                   are launched in row chunks of about this many
+                                   bytes (see Chunks) */
 } gb_engine_config;
 
 typedef struct {

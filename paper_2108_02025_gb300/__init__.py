@@ -391,7 +391,8 @@ class EngineConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("streams", ctypes.c_int32),
                 ("max_inflight", ctypes.c_int32), ("max_step_requests", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("sim_bytes_per_ns", ctypes.c_double),
-                ("table", ctypes.c_void_p), ("pool_elems", ctypes.c_int64), ("pool_seed", ctypes.c_uint64)]
+                ("table", ctypes.c_void_p), ("pool_elems", ctypes.c_int64), ("pool_seed", ctypes.c_uint64),
+                ("chunk_bytes", ctypes.c_size_t)]
 
 
 class Request(ctypes.Structure):
@@ -458,11 +459,12 @@ class Engine:
     submitted with ``pool=True`` read their inputs from them."""
 
     def __init__(self, budget_bytes, streams=4, max_inflight=4096, max_step_requests=256,
-                 host_only=False, sim_bytes_per_ns=1000.0, table=None, pool_elems=0, pool_seed=0):
+                 host_only=False, sim_bytes_per_ns=1000.0, table=None, pool_elems=0, pool_seed=0,
+                 chunk_bytes=0):
         self.table = table
         cfg = EngineConfig(budget_bytes, streams, max_inflight, max_step_requests,
                            ENGINE_HOST_ONLY if host_only else 0, sim_bytes_per_ns,
-                           _addr(table) if table is not None else None, pool_elems, pool_seed)
+                           _addr(table) if table is not None else None, pool_elems, pool_seed, chunk_bytes)
         h = ctypes.c_void_p()
         _check(gb_engine_create(cfg, ctypes.addressof(h)), "engine_create")
         self.h = h.value

@@ -17,6 +17,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <set>
 #include <thread>
 #include <vector>
 
@@ -91,9 +92,10 @@ __device__ __forceinline__ uint16_t bf16_bits(float v) {
 
 // Block b works on chunk b - first[s] of segment s, the last s with
 // first[s] <= b: four consecutive elements per thread and step, 16-byte
-// (FP32) or 8-byte (BF16) accesses.  dst and src start 16-byte aligned
-// (arena pieces 256 bytes, pool operands 32 bytes), GER rows too (ld a
-// multiple of 4), so a group of four never straddles a row.
+// (FP32) or 8-byte (BF16) accesses.  Fill and GER segments start 16-byte
+// aligned (arena pieces 256 bytes, pool operands 32 bytes, GER rows ld a
+// multiple of 4 elements apart), so a group of four never straddles a row;
+// a copy of the c of a row chunk may start anywhere.
 __global__ void __launch_bounds__(kThreads) operand_kernel(const OperandSeg* __restrict__ segs,
                                                            const int64_t* __restrict__ first, int nseg) {
   const int64_t b = blockIdx.x;
@@ -130,9 +132,12 @@ __global__ void __launch_bounds__(kThreads) operand_kernel(const OperandSeg* __r
       }
     }
   } else if (sg.kind == kCopyF32) {
+    // a chunk of rows starts at any element: 16-byte accesses only when
+    // both ends are 16-byte aligned
     float* d = static_cast<float*>(sg.dst);
+    const bool wide = ((reinterpret_cast<uintptr_t>(d) | reinterpret_cast<uintptr_t>(sg.src)) & 15) == 0;
     for (int64_t e = e0 + 4 * (int64_t)threadIdx.x; e < e1; e += 4 * kThreads) {
-      if (e + 4 <= e1) {
+      if (wide && e + 4 <= e1) {
         *reinterpret_cast<float4*>(d + e) = __ldcs(reinterpret_cast<const float4*>(sg.src + e));
       } else {
         for (int q = 0; q < 4 && e + q < e1; ++q) d[e + q] = sg.src[e + q];
@@ -310,7 +315,22 @@ struct Req {
   unsigned char* base = nullptr;  // device address of the range (host-only: nullptr)
   int64_t admit_ns = 0, launch_ns = 0, done_ns = 0, step = -1;
   int status = GB_OK;
+  // Launch in row chunks (GEMV and GER on the pool, larger than the chunk
+  // size): rows launched so far, parts whose step has not retired, and the
+  // (slot, step) of every part launched.
+  int64_t rows = 1, rows_launched = 0, row_bytes = 0;
+  bool chunked = false;
+  int parts_out = 0;
+  std::vector<std::pair<int, int64_t>> part_steps;
   unsigned char* ptr(int i) const { return base + f.p[i].off; }
+};
+
+// Rows [row0, row0 + rows) of a request, launched in one step; `last` is
+// the part that completes the request's rows (its step copies the result).
+struct Part {
+  Req* q;
+  int64_t row0, rows;
+  bool last;
 };
 
 constexpr int64_t kSpinNs = 200000;  // the worker polls instead of sleeping this close to an arrival
@@ -334,7 +354,7 @@ struct Slot {
   int64_t sim_done_ns = 0;  // host-only mode
   bool failed = false;
   int fail_status = GB_OK;
-  std::vector<Req*> reqs;
+  std::vector<Part> parts;
 };
 
 }  // namespace
@@ -373,7 +393,7 @@ struct gb_engine {
   bool retire();
   bool admit();
   bool launch();
-  int launch_step(Slot& s, std::vector<Req*>& reqs);
+  int launch_step(Slot& s, const std::vector<Part>& parts);
   int ensure_capacity(Slot& s, size_t bytes);
   void finish(Slot& s, int64_t t, int status);
 };
@@ -402,27 +422,31 @@ bool gb_engine::retire() {
   return any;
 }
 
+// A step has retired: its parts are done.  A request completes when all its
+// rows have been launched and no part of it is still on the GPU.
 void gb_engine::finish(Slot& s, int64_t t, int status) {
   std::vector<gb_completion> out;
-  out.reserve(s.reqs.size());
-  for (Req* q : s.reqs) {
+  for (const Part& pt : s.parts) {
+    Req* q = pt.q;
+    if (status != GB_OK && q->status == GB_OK) q->status = status;
+    if (--q->parts_out > 0 || q->rows_launched < q->rows) continue;
     q->done_ns = t;
     arena.release(q->off, q->f.total);
     gb_completion c{};
     c.id = q->r.id;
-    c.status = status;
+    c.status = q->status;
     c.op = q->r.op;
     c.arrival_ns = q->r.arrival_ns;
     c.admitted_ns = q->admit_ns;
     c.launched_ns = q->launch_ns;
     c.done_ns = t;
-    c.step = s.index;
+    c.step = q->step;
     c.bytes = (int64_t)q->f.total;
     out.push_back(c);
     delete q;
+    --inflight;
   }
-  inflight -= (int64_t)s.reqs.size();
-  s.reqs.clear();
+  s.parts.clear();
   s.busy = false;
   s.failed = false;
   bytes_in_use = arena.used();
@@ -480,7 +504,7 @@ int gb_engine::ensure_capacity(Slot& s, size_t bytes) {
 // generator; for pool requests the copies of the initial outputs and the
 // GERs), one batched launch for the GEMVs and DOTs (and the GERs of drawn
 // requests), result copies, event.
-int gb_engine::launch_step(Slot& s, std::vector<Req*>& reqs) {
+int gb_engine::launch_step(Slot& s, const std::vector<Part>& parts) {
   std::vector<OperandSeg> segs;
   auto fill = [&](void* dst, int64_t count, uint64_t key, int32_t kind) {
     OperandSeg g{};
@@ -490,29 +514,31 @@ int gb_engine::launch_step(Slot& s, std::vector<Req*>& reqs) {
     g.kind = kind;
     segs.push_back(g);
   };
-  for (Req* q : reqs) {
+  for (const Part& pt : parts) {
+    const Req* q = pt.q;
     const gb_request& r = q->r;
     const uint64_t seed = r.seed;
-    if (pooled(r)) {
+    if (pooled(r)) {  // rows [row0, row0 + rows) of the output
       const float* P = pool_f32;
       OperandSeg g{};
-      g.dst = q->ptr(0);
       if (r.op == GB_REQ_GER) {
-        g.src = P + q->pool_off[0];
-        g.x = P + q->pool_off[1];
+        g.dst = reinterpret_cast<float*>(q->ptr(0)) + pt.row0 * q->f.ld;
+        g.src = P + q->pool_off[0] + pt.row0 * q->f.ld;
+        g.x = P + q->pool_off[1] + pt.row0;
         g.y = P + q->pool_off[2];
-        g.count = r.m * q->f.ld;
+        g.count = pt.rows * q->f.ld;
         g.key = (uint64_t)q->f.ld;
         g.kind = kGerF32;
         g.n = (int32_t)r.n;
         g.alpha = r.alpha;
       } else {
-        g.src = P + q->pool_off[2];
-        g.count = r.op == GB_REQ_GEMV ? r.m : 1;
+        g.dst = reinterpret_cast<float*>(q->ptr(0)) + pt.row0;
+        g.src = P + q->pool_off[2] + pt.row0;
+        g.count = pt.rows;
         g.kind = kCopyF32;
       }
       segs.push_back(g);
-    } else if (r.op == GB_REQ_GEMV) {
+    } else if (r.op == GB_REQ_GEMV) {  // drawn requests are never split
       fill(q->ptr(0), r.m * q->f.ld, stream_key(seed, 1), r.form == GB_FORM_BF16 ? kFillBF16 : kFillF32);
       fill(q->ptr(1), r.n, stream_key(seed, 2), kFillF32);
       fill(q->ptr(2), r.m, stream_key(seed, 3), kFillF32);
@@ -533,8 +559,9 @@ int gb_engine::launch_step(Slot& s, std::vector<Req*>& reqs) {
   // every GEMV (FP32 or BF16 A) and DOT (a one-row FP32 GEMV) in one
   // batched launch, with the GERs of drawn requests
   std::vector<BatchItem> items;
-  items.reserve(reqs.size());
-  for (Req* q : reqs) {
+  items.reserve(parts.size());
+  for (const Part& pt : parts) {
+    const Req* q = pt.q;
     const gb_request& r = q->r;
     const bool pool = pooled(r);
     if (pool && r.op == GB_REQ_GER) continue;  // done by the operand kernel
@@ -544,13 +571,13 @@ int gb_engine::launch_step(Slot& s, std::vector<Req*>& reqs) {
     if (pool) {
       const float* P = pool_f32;
       it.kind = r.op == GB_REQ_GEMV && r.form == GB_FORM_BF16 ? kBatchGemvBF16 : kBatchGemvF32;
-      it.m = r.op == GB_REQ_GEMV ? r.m : 1;
+      it.m = r.op == GB_REQ_GEMV ? pt.rows : 1;
       it.alpha = r.op == GB_REQ_GEMV ? r.alpha : 1.0f;
-      // GEMV kinds only read A
-      it.A = it.kind == kBatchGemvBF16 ? static_cast<void*>(pool_bf16 + q->pool_off[0])
-                                       : static_cast<void*>(pool_f32 + q->pool_off[0]);
+      // GEMV kinds only read A; rows [row0, row0 + rows)
+      const int64_t a0 = q->pool_off[0] + pt.row0 * q->f.ld;
+      it.A = it.kind == kBatchGemvBF16 ? static_cast<void*>(pool_bf16 + a0) : static_cast<void*>(pool_f32 + a0);
       it.x = P + q->pool_off[1];
-      it.c = reinterpret_cast<float*>(q->ptr(0));
+      it.c = reinterpret_cast<float*>(q->ptr(0)) + pt.row0;
     } else if (r.op == GB_REQ_GEMV) {
       it.kind = r.form == GB_FORM_BF16 ? kBatchGemvBF16 : kBatchGemvF32;
       it.m = r.m;
@@ -599,9 +626,17 @@ int gb_engine::launch_step(Slot& s, std::vector<Req*>& reqs) {
     if (cudaPeekAtLastError() != cudaSuccess) return GB_ERR_CUDA;
   }
   if (nb > 0 && gb_sgemv_batch(s.host + o_plan, s.dev + o_plan, sm) != GB_OK) return GB_ERR_CUDA;
-  for (Req* q : reqs) {
+  for (const Part& pt : parts) {
+    const Req* q = pt.q;
     const gb_request& r = q->r;
-    if (!r.out) continue;
+    if (!r.out || !pt.last) continue;
+    // the result is whole once the request's earlier parts, on other
+    // streams, are done too
+    for (const auto& ps : q->part_steps) {
+      const Slot& o = slots[(size_t)ps.first];
+      if (&o != &s && o.busy && o.index == ps.second && !o.failed)
+        if (cudaStreamWaitEvent(sm, o.done, 0) != cudaSuccess) return GB_ERR_CUDA;
+    }
     cudaError_t e;
     const unsigned char* res = pooled(r) || r.op == GB_REQ_GER ? q->ptr(0) : q->ptr(2);
     if (r.op == GB_REQ_GER)
@@ -615,28 +650,72 @@ int gb_engine::launch_step(Slot& s, std::vector<Req*>& reqs) {
   return GB_OK;
 }
 
-// Launch the admitted requests as a step on a free slot.
+// Launch admitted requests as a step on a free slot.  Whole requests first,
+// in admission order (at most max_step_requests); then, with a chunk size
+// set, row chunks of the chunked requests in admission order until the step
+// holds chunk_bytes of their work, so a large request never holds the GPU
+// for longer than a chunk while smaller ones wait behind it.
 bool gb_engine::launch() {
   if (admitted.empty()) return false;
   Slot* s = nullptr;
-  int busy = 0;
-  for (Slot& x : slots) {
-    if (x.busy) ++busy;
-    else if (!s) s = &x;
+  int busy = 0, slot = -1;
+  for (size_t i = 0; i < slots.size(); ++i) {
+    if (slots[i].busy) ++busy;
+    else if (!s) {
+      s = &slots[i];
+      slot = (int)i;
+    }
   }
   if (!s) return false;
-  const size_t k = std::min(admitted.size(), (size_t)cfg.max_step_requests);
-  s->reqs.assign(admitted.begin(), admitted.begin() + (long)k);
-  admitted.erase(admitted.begin(), admitted.begin() + (long)k);
+  std::vector<Part> parts;
+  size_t whole = 0;
+  for (auto it = admitted.begin(); it != admitted.end() && whole < (size_t)cfg.max_step_requests;) {
+    Req* q = *it;
+    if (q->chunked) {
+      ++it;
+      continue;
+    }
+    parts.push_back(Part{q, 0, q->rows, true});
+    q->rows_launched = q->rows;
+    ++whole;
+    it = admitted.erase(it);
+  }
+  int64_t room = (int64_t)cfg.chunk_bytes;
+  for (auto it = admitted.begin(); it != admitted.end() && room > 0;) {
+    Req* q = *it;
+    if (!q->chunked) {
+      ++it;
+      continue;
+    }
+    const int64_t left = q->rows - q->rows_launched;
+    int64_t take = room / q->row_bytes;
+    if (take < 1) take = 1;
+    if (take > left) take = left;
+    parts.push_back(Part{q, q->rows_launched, take, q->rows_launched + take == q->rows});
+    q->rows_launched += take;
+    room -= take * q->row_bytes;
+    if (q->rows_launched == q->rows) it = admitted.erase(it);
+    else ++it;
+  }
+  if (parts.empty()) return false;
+  s->parts = parts;
   s->index = steps++;
   s->busy = true;
   if (busy + 1 > steps_inflight_peak.load()) steps_inflight_peak = busy + 1;
   const int64_t t = now_ns();
   size_t bytes = 0;
-  for (Req* q : s->reqs) {
-    q->launch_ns = t;
+  int64_t after = 0;  // host-only: the step ends after the earlier parts of its requests
+  for (const Part& pt : s->parts) {
+    Req* q = pt.q;
+    if (q->parts_out == 0 && q->step < 0) q->launch_ns = t;
     q->step = s->index;
-    bytes += q->f.total;
+    ++q->parts_out;
+    bytes += q->chunked ? (size_t)(pt.rows * q->row_bytes) : q->f.total;
+    if (pt.last)
+      for (const auto& ps : q->part_steps)
+        if (slots[(size_t)ps.first].busy && slots[(size_t)ps.first].index == ps.second)
+          after = std::max(after, slots[(size_t)ps.first].sim_done_ns);
+    q->part_steps.emplace_back(slot, s->index);
   }
   if (fault_injected(kInjectStep)) {
     s->failed = true;
@@ -644,10 +723,10 @@ bool gb_engine::launch() {
     return true;
   }
   if (host_only) {
-    s->sim_done_ns = t + (int64_t)((double)bytes / cfg.sim_bytes_per_ns);
+    s->sim_done_ns = std::max(after, t + (int64_t)((double)bytes / cfg.sim_bytes_per_ns));
     return true;
   }
-  const int st = launch_step(*s, s->reqs);
+  const int st = launch_step(*s, s->parts);
   if (st != GB_OK) {
     // nothing more is enqueued on this stream; let what was enqueued finish
     cudaStreamSynchronize(s->stream);
@@ -830,6 +909,13 @@ int gb_engine_submit(gb_engine* e, const gb_request* r) {
     delete q;
     return GB_ERR_BUDGET;
   }
+  q->rows = r->op == GB_REQ_DOT ? 1 : r->m;
+  if (pooled(*r) && r->op != GB_REQ_DOT && e->cfg.chunk_bytes > 0) {
+    // bytes a row moves: the A row and c (GEMV), the C0 and C rows (GER)
+    const int64_t eb = r->op == GB_REQ_GEMV && r->form == GB_FORM_BF16 ? 2 : 4;
+    q->row_bytes = r->op == GB_REQ_GEMV ? q->f.ld * eb + 8 : q->f.ld * 8;
+    q->chunked = q->row_bytes * q->rows > (int64_t)e->cfg.chunk_bytes;
+  }
   if (q->r.arrival_ns == 0) q->r.arrival_ns = now_ns();
   {
     std::lock_guard<std::mutex> lk(e->mu);
@@ -887,16 +973,17 @@ void gb_engine_destroy(gb_engine* e) {
   }
   e->cv_work.notify_all();
   if (e->worker.joinable()) e->worker.join();
-  for (Req* q : e->pending) delete q;
+  std::set<Req*> owned(e->pending.begin(), e->pending.end());
+  owned.insert(e->admitted.begin(), e->admitted.end());
   for (Slot& s : e->slots) {
     if (s.stream) cudaStreamSynchronize(s.stream);
-    for (Req* q : s.reqs) delete q;
+    for (const Part& pt : s.parts) owned.insert(pt.q);
     if (s.done) cudaEventDestroy(s.done);
     if (s.stream) cudaStreamDestroy(s.stream);
     if (s.host) cudaFreeHost(s.host);
     if (s.dev) cudaFree(s.dev);
   }
-  for (Req* q : e->admitted) delete q;
+  for (Req* q : owned) delete q;
   if (e->arena_base) cudaFree(e->arena_base);
   if (e->pool_f32) cudaFree(e->pool_f32);
   if (e->pool_bf16) cudaFree(e->pool_bf16);

@@ -209,3 +209,52 @@ def test_pool_offsets_stay_inside_the_pool_and_are_aligned():
             assert o % 8 == 0 and 0 <= o and o + L <= P
     offs = {synth.pool_offset(seed, 1, 1000, P) for seed in range(200)}
     assert len(offs) > 150, "operands of different requests start at different places"
+
+
+def test_chunks_let_small_requests_pass_large_ones():
+    """With chunk_bytes set, a large pool GEMV or GER is launched a chunk of
+    rows at a time; small requests that arrive after it run between its
+    chunks and complete long before it, and it completes once, with every
+    row launched."""
+    P = 1 << 26
+    chunk = 4 * MB
+    with gb.Engine(1 << 30, streams=2, max_inflight=1000, max_step_requests=64, host_only=True,
+                   sim_bytes_per_ns=10.0, pool_elems=P, chunk_bytes=chunk) as e:
+        t0 = e.now_ns() + 5_000_000
+        assert e.submit(0, gb.REQ_GEMV, 4096, 4096, pool=True, arrival_ns=t0) == gb.GB_OK      # 64 MB
+        assert e.submit(1, gb.REQ_GER, 2048, 4096, pool=True, arrival_ns=t0 + 1) == gb.GB_OK   # 64 MB
+        for i in range(2, 40):
+            assert e.submit(i, gb.REQ_GEMV, 64, 64, pool=True, arrival_ns=t0 + 200_000 * i) == gb.GB_OK
+        assert e.drain(60000) == gb.GB_OK
+        done = {c["id"]: c for c in e.poll()}
+        st = e.stats()
+    assert len(done) == 40 and all(c["status"] == gb.GB_OK for c in done.values())
+    assert st["steps"] >= 2 * (64 * MB // chunk), "the large requests went in chunks"
+    assert st["bytes_in_use"] == 0 and st["inflight_peak"] <= 40
+    big_done = min(done[0]["done_ns"], done[1]["done_ns"])
+    small = [done[i] for i in range(2, 40) if done[i]["arrival_ns"] < big_done - 2_000_000]
+    assert len(small) > 5
+    assert all(c["done_ns"] < big_done for c in small), "small requests overtake the chunked ones"
+    for c in done.values():
+        assert c["arrival_ns"] <= c["admitted_ns"] <= c["launched_ns"] <= c["done_ns"]
+
+
+def test_chunked_request_with_a_failed_chunk_completes_with_the_error():
+    code = textwrap.dedent("""
+        import sys
+        sys.path.insert(0, %r)
+        import paper_2108_02025_gb300 as gb
+        with gb.Engine(1 << 30, streams=2, host_only=True, sim_bytes_per_ns=100.0, pool_elems=1 << 24,
+                       chunk_bytes=1 << 20) as e:
+            assert e.submit(0, gb.REQ_GER, 1024, 1024, pool=True) == 0        # 8 MB: 8 chunks
+            assert e.drain(20000) == 0
+            assert e.submit(1, gb.REQ_GEMV, 32, 32, pool=True) == 0
+            assert e.drain(20000) == 0
+            done = sorted(e.poll(), key=lambda c: c["id"])
+            st = e.stats()
+            print([c["status"] for c in done], st["failed"], st["steps"], st["bytes_in_use"])
+    """ % ROOT)
+    env = dict(os.environ, GB_FAULT_INJECT="step:3")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == "[-103, 0] 1 9 0"

@@ -216,10 +216,10 @@ def check_pool(req, got):
         assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), req
 
 
-def serve_pool(reqs, offsets, budget=1 << 30, streams=4, max_step=256):
+def serve_pool(reqs, offsets, budget=1 << 30, streams=4, max_step=256, chunk_bytes=0):
     outs = []
     with gb.Engine(budget, streams=streams, max_inflight=4096, max_step_requests=max_step,
-                   pool_elems=POOL, pool_seed=POOL_SEED) as e:
+                   pool_elems=POOL, pool_seed=POOL_SEED, chunk_bytes=chunk_bytes) as e:
         assert e.stats()["pool_bytes"] == POOL * 6
         t0 = e.now_ns() + 50_000_000
         for i, (op, form, m, n, alpha, seed) in enumerate(reqs):
@@ -284,3 +284,27 @@ def test_pool_refusals():
         assert e.stats()["submitted"] == 0
     with gb.Engine(1 << 30) as e:
         assert e.submit(0, gb.REQ_GEMV, 8, 8, pool=True) == -2            # no pool
+
+
+def test_pool_chunks_against_oracle_and_bit_identical_to_whole():
+    """Row chunks of 64 KB (most GEMVs and GERs of the stream split into
+    several steps, on several streams): every result against the oracle and
+    bit-identical to the same request served whole and alone."""
+    reqs, t = stream(80, 6, rate=100000.0)
+    chunked, done, stats = serve_pool(reqs, t, chunk_bytes=64 << 10)
+    assert stats["steps"] > 80
+    for r, o in zip(reqs, chunked):
+        check_pool(r, o)
+    for i in (0, 3, 9, 17, 33, 51, 79):
+        whole, _, _ = serve_pool([reqs[i]], [0], streams=1)
+        assert np.array_equal(whole[0].view(np.uint32), chunked[i].view(np.uint32)), reqs[i]
+
+
+def test_pool_chunks_of_one_row():
+    """chunk_bytes below one row: every chunk is a single row."""
+    reqs = [(gb.REQ_GEMV, gb.FORM_F32, 37, 300, 0.5, 700), (gb.REQ_GER, gb.FORM_F32, 29, 301, -2.0, 701),
+            (gb.REQ_GEMV, gb.FORM_BF16, 41, 999, 1.0, 702), (gb.REQ_DOT, gb.FORM_F32, 1, 5000, 1.0, 703)]
+    outs, done, stats = serve_pool(reqs, [0, 0, 0, 0], chunk_bytes=16)
+    assert stats["steps"] >= 41
+    for r, o in zip(reqs, outs):
+        check_pool(r, o)
