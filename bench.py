@@ -918,6 +918,47 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def measure_link(device, nbytes=1 << 30, reps=3):
+    """GB/s of this machine's host link as the e2e leg uses it: a copy-engine
+    upload from pinned memory, a gb_copy_to_host download, and both at once
+    on two streams (best of `reps`)."""
+    import torch
+    import paper_2108_02025_gb300 as gb
+    h_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h_out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d_in = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    d_out = torch.zeros(nbytes, dtype=torch.uint8, device=device)
+    s1, s2 = torch.cuda.Stream(device), torch.cuda.Stream(device)
+
+    def up():
+        with torch.cuda.stream(s1):
+            d_in.copy_(h_in, non_blocking=True)
+
+    def down():
+        if gb.gb_copy_to_host(h_out, d_out, nbytes, s2) != gb.GB_OK:
+            raise RuntimeError("gb_copy_to_host failed")
+
+    def best(fns, moved):
+        t = []
+        for _ in range(reps + 1):
+            torch.cuda.synchronize(device)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s1)
+            s2.wait_event(e0)
+            for f in fns:
+                f()
+            s1.wait_stream(s2)
+            e1.record(s1)
+            torch.cuda.synchronize(device)
+            t.append(e0.elapsed_time(e1) / 1e3)
+        return moved / min(t[1:]) / 1e9
+
+    out = {"h2d_GB_s": round(best([up], nbytes), 1), "d2h_GB_s": round(best([down], nbytes), 1),
+           "both_GB_s": round(best([up, down], 2 * nbytes), 1)}
+    del h_in, h_out, d_in, d_out
+    return out
+
+
 def run_e2e(wl, stream, device, bytes_step, args, world):
     """The same step through host buffers: every step copies all its inputs
     from pinned host memory to the device (copy engine), runs the 18 calls
@@ -977,9 +1018,16 @@ def run_e2e(wl, stream, device, bytes_step, args, world):
     secs = max_over_ranks(e0.elapsed_time(e1) / 1e3, device)
     del wls[1]
     torch.cuda.empty_cache()
-    return {"value": round(whole_job_value(bytes_step, steps, world, secs), 1), "unit": "GB/s",
+    link = measure_link(device)
+    # no step can beat the link: max(upload alone, download alone, both at once)
+    t_min = max(h2d / (link["h2d_GB_s"] * 1e9), d2h / (link["d2h_GB_s"] * 1e9),
+                (h2d + d2h) / (link["both_GB_s"] * 1e9))
+    value = whole_job_value(bytes_step, steps, world, secs)
+    link["bound_GB_s"] = round(bytes_step / t_min / 1e9, 1)
+    link["frac"] = round(value / world / link["bound_GB_s"], 3)
+    return {"value": round(value, 1), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
-            "ms_per_step": round(secs / steps * 1e3, 3),
+            "ms_per_step": round(secs / steps * 1e3, 3), "link": link,
             "note": "two device buffer sets: uploads (copy engine), calls and downloads (gb_copy_to_host "
                     "kernel) of consecutive steps overlap"}
 
