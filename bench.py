@@ -45,6 +45,7 @@ SQ, TALL, WIDE = (16384, 16384), (1048576, 64), (64, 1048576)
 NDOT = 1 << 28
 HBM_FALLBACK_GBS = 6800.0
 CPU_FRACTION = 16    # cpu_baseline sample: 1/16 of a step
+NOMINAL_HBM_GBS = 8000.0   # HBM3e data-sheet bandwidth, for a second fraction beside the measured peak
 REF_FRACTION = 32    # reference arm: 1/32 of a step per step
 SMS, DP_FMA_PER_CLK_SM, SM_MAX_MHZ = 152, 2, 2070.0   # FP64 pipe: 2 FMA/clk/SM (1.26 TFLOP/s at 2.07 GHz)
 
@@ -848,8 +849,11 @@ def run_ours(args):
     ops_report = []
     for i, (name, kind, dt, lay, m, n) in enumerate(ops):
         gbs = alg_bytes(kind, dt, m, n) / op_times[i] / 1e9
-        ops_report.append({"op": name, "us": round(op_times[i] * 1e6, 2), "GB_s": round(gbs, 1),
-                           "frac_hbm": round(gbs / hbm, 4)})
+        each = sorted(per_op[k][i][0].elapsed_time(per_op[k][i][1]) * 1e3 for k in range(args.steps))
+        ops_report.append({"op": name, "us": round(op_times[i] * 1e6, 2),
+                           "us_median": round(each[len(each) // 2], 2), "us_min": round(each[0], 2),
+                           "GB_s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4),
+                           "frac_nominal": round(gbs / NOMINAL_HBM_GBS, 4)})
 
     e2e = None
     if not args.no_e2e:
