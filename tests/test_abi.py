@@ -98,6 +98,12 @@ def test_ger_validation(f):
     assert g(0, 0, 4, 1.0, None, None, None, 4, 0) == 0
 
 
+def test_copy_to_host_validation():
+    assert gb.gb_copy_to_host(None, None, 0, 0) == gb.GB_OK     # nothing to copy
+    assert gb.gb_copy_to_host(None, P, 64, 0) == -1              # no destination
+    assert gb.gb_copy_to_host(Q, None, 64, 0) == -2              # no source
+
+
 def test_workspace_bytes():
     wb = gb.gb_workspace_bytes
     assert wb(gb.OP_GER, gb.F64, 0, 1000, 1000) == 0
