@@ -23,12 +23,13 @@
  * of pool requests and computes their GERs), one persistent launch (the
  * batched kernel of gb_sgemv_batch) for all the step's GEMVs (FP32 or BF16
  * A), DOTs (one-row GEMVs) and the GERs of drawn requests, then the copies
- * of the results to the requests' host buffers and an event.  GEMV and DOT sums are FP32 fma chains of at most 64 products in a
- * compensated FP32 sum; GER is one fma per element.
- * Requests that arrive while steps are on the GPU are admitted and launched
- * in the next step on another stream, so steps overlap on the device.  When
- * a step's event completes, its requests complete, their memory returns to
- * the arena and more requests are admitted.
+ * of the results to the requests' host buffers and an event.  GEMV and DOT
+ * sums are FP32 fma chains of at most 64 products in a compensated FP32
+ * sum; GER is one fma per element.  Requests that arrive while steps are
+ * on the GPU are admitted and launched in the next step on another stream,
+ * so steps overlap on the device.  When a step's event completes, its
+ * requests complete (a request in chunks once all its chunks are done),
+ * their memory returns to the arena and more requests are admitted.
  *
  * Operands.  A request's inputs are drawn on the device from the counter-
  * based SplitMix64 generator (Steele, Lea and Flood, OOPSLA 2014) with the
@@ -59,9 +60,10 @@
  *
  * Chunks (chunk_bytes > 0).  A step takes the admitted requests that are
  * launched whole first, in admission order, then rows of the chunked
- * requests (GB_REQ_POOL GEMVs and GERs whose rows move more than
- * chunk_bytes: the A row and c element, or the C0 and C rows) in admission
- * order, at least one row and at most about chunk_bytes of them per step.
+ * requests (GB_REQ_POOL GEMVs and GERs that move more than chunk_bytes in
+ * all, counting per row the A row and the c element, or the C0 and C rows)
+ * in admission order, at least one row and about chunk_bytes of them per
+ * step.
  * A large request then holds the GPU a chunk at a time, so smaller requests
  * that arrive meanwhile run between its chunks.  Rows are independent
  * (each row's sum, or each element, is computed as it would be whole), so
@@ -86,8 +88,9 @@
  * and failure handling without a GPU.
  *
  * Fault injection (host side): GB_FAULT_INJECT=step:<k> makes the k-th step
- * (1-based) complete without being launched: its requests complete with
- * status GB_ERR_INJECTED and the engine goes on.
+ * (1-based) complete without being launched: its requests (a request in
+ * chunks once its other chunks are done) complete with status
+ * GB_ERR_INJECTED and the engine goes on.
  */
 #ifndef GBSERVE_H
 #define GBSERVE_H
