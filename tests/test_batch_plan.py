@@ -328,6 +328,17 @@ def test_mixed_items_argument_checks():
     bad = items_of(ok)
     bad[0].x = bad[1].x          # two readers of one vector are fine
     assert gb.gb_batch_plan(2, bad, None, buf, nb) == gb.GB_OK
+    # GEMVs reading overlapping windows of one resident operand pool (the
+    # serving engine's pool requests): shared A and x, distinct outputs
+    pool = items_of([(gb.BATCH_GEMV_F32, 10, 10, 12, 1.0)] * 3)
+    for k in (1, 2):
+        pool[k].A = pool[0].A + 16 * k
+        pool[k].x = pool[0].x + 32 * k
+    nb3 = gb.gb_batch_plan_bytes(3, pool, None)
+    buf3 = aligned_buffer(nb3)
+    assert gb.gb_batch_plan(3, pool, None, buf3, nb3) == gb.GB_OK
+    pool[2].c = pool[1].c + 4    # two outputs overlapping: refused
+    assert gb.gb_batch_plan(3, pool, None, buf3, nb3) == -2
     assert gb.gb_batch_plan(2, arr, gb.tuning_table({4: (4, 3, 65536)}), buf, nb) == -3
     assert gb.gb_batch_plan(2, arr, None, buf[1:], nb) == -4
     assert gb.gb_batch_plan(2, arr, None, buf, nb - 16) == -5
