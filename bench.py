@@ -17,6 +17,15 @@ call starts with its operand in L2.  The metric is algorithmic HBM bytes
 step; per-operation figures and the roofline of the dominant kernel are
 reported beside it.
 
+Beside the device-timed value the line carries: `e2e` (the same step with
+inputs uploaded from pinned host memory and results downloaded every step,
+with the host link measured in the same run and the step bound it sets),
+`cpu_baseline` (the CPU oracle on a bounded sample: all cores, one core,
+and the compensated oracle), and the growth legs `precision` (BF16 / E4M3
+GEMV), `batched` (4096 GEMVs in one persistent launch) and `serving` (the
+engine on resident operand pools: saturated throughput, p50 / p99 at 50%,
+80% and 95% load, and the same stream with operands drawn per request).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank runs its own replica on its own GPU (the operations
 do not shard: "replicas only"); the step time is the maximum over ranks.
