@@ -219,7 +219,7 @@ def test_chunks_let_small_requests_pass_large_ones():
     P = 1 << 26
     chunk = 4 * MB
     with gb.Engine(1 << 30, streams=2, max_inflight=1000, max_step_requests=64, host_only=True,
-                   sim_bytes_per_ns=10.0, pool_elems=P, chunk_bytes=chunk) as e:
+                   sim_bytes_per_ns=4.0, pool_elems=P, chunk_bytes=chunk) as e:
         t0 = e.now_ns() + 5_000_000
         assert e.submit(0, gb.REQ_GEMV, 4096, 4096, pool=True, arrival_ns=t0) == gb.GB_OK      # 64 MB
         assert e.submit(1, gb.REQ_GER, 2048, 4096, pool=True, arrival_ns=t0 + 1) == gb.GB_OK   # 64 MB
@@ -232,7 +232,7 @@ def test_chunks_let_small_requests_pass_large_ones():
     assert st["steps"] >= 2 * (64 * MB // chunk), "the large requests went in chunks"
     assert st["bytes_in_use"] == 0 and st["inflight_peak"] <= 40
     big_done = min(done[0]["done_ns"], done[1]["done_ns"])
-    small = [done[i] for i in range(2, 40) if done[i]["arrival_ns"] < big_done - 3_000_000]
+    small = [done[i] for i in range(2, 40) if done[i]["arrival_ns"] < big_done - 2_500_000]
     assert len(small) > 5
     assert all(c["done_ns"] <= big_done for c in small), "small requests overtake the chunked ones"
     for c in done.values():
