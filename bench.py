@@ -972,6 +972,15 @@ def measure_link(device, nbytes=1 << 30, reps=3):
     return out
 
 
+def link_bound(bytes_step, h2d, d2h, link):
+    """GB/s of algorithmic bytes that a step moving h2d bytes up and d2h
+    bytes down cannot beat: its time is at least the upload alone, the
+    download alone, and both at the rate the link reaches both ways."""
+    t_min = max(h2d / (link["h2d_GB_s"] * 1e9), d2h / (link["d2h_GB_s"] * 1e9),
+                (h2d + d2h) / (link["both_GB_s"] * 1e9))
+    return bytes_step / t_min / 1e9
+
+
 def run_e2e(wl, stream, device, bytes_step, args, world):
     """The same step through host buffers: every step copies all its inputs
     from pinned host memory to the device (copy engine), runs the 18 calls
@@ -1032,11 +1041,8 @@ def run_e2e(wl, stream, device, bytes_step, args, world):
     del wls[1]
     torch.cuda.empty_cache()
     link = measure_link(device)
-    # no step can beat the link: max(upload alone, download alone, both at once)
-    t_min = max(h2d / (link["h2d_GB_s"] * 1e9), d2h / (link["d2h_GB_s"] * 1e9),
-                (h2d + d2h) / (link["both_GB_s"] * 1e9))
     value = whole_job_value(bytes_step, steps, world, secs)
-    link["bound_GB_s"] = round(bytes_step / t_min / 1e9, 1)
+    link["bound_GB_s"] = round(link_bound(bytes_step, h2d, d2h, link), 1)
     link["frac"] = round(value / world / link["bound_GB_s"], 3)
     return {"value": round(value, 1), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,

@@ -100,3 +100,16 @@ def test_source_sha_ignores_comments_only():
     b = "/* header */\nint f(int x) {\n\n  return 2 * x;\n}  // end\n"
     c = "int f(int x) { return 3 * x; }"
     assert bench.code_of(a) == bench.code_of(b) != bench.code_of(c)
+
+
+def test_link_bound():
+    """The e2e step bound: the slowest of upload alone, download alone and
+    both directions at their shared rate (figures of a GB300 machine)."""
+    link = {"h2d_GB_s": 210.7, "d2h_GB_s": 193.0, "both_GB_s": 299.2}
+    b = bench.link_bound(29.07e9, 17.74e9, 6.455e9, link)
+    assert abs(b - 29.07e9 / (17.74e9 / 210.7e9) / 1e9) < 1e-6        # the upload decides
+    assert abs(b - 345.3) < 0.5
+    up_only = bench.link_bound(10e9, 10e9, 0, link)
+    assert abs(up_only - 210.7) < 1e-9
+    both = bench.link_bound(10e9, 5e9, 5e9, {"h2d_GB_s": 100.0, "d2h_GB_s": 100.0, "both_GB_s": 100.0})
+    assert abs(both - 100.0) < 1e-9                                     # the shared rate decides
