@@ -5,7 +5,12 @@ The functions ``gb_*`` have the names and argument order of the C ABI in
 pointers, a ``torch.cuda.Stream`` becomes its handle, and the C status code
 is returned unchanged.  ``gemv``, ``dot`` and ``ger`` are convenience calls
 over them that pick the dtype variant, hold a zeroed workspace per device
-and stream, and raise ``GbError`` on a non-zero status.
+and stream, and raise ``GbError`` on a non-zero status; ``quantize`` and
+``gemv_q`` do the same for BF16 / E4M3 storage of A.  ``Batch`` plans and
+launches many GEMVs (and GERs) as one persistent kernel, optionally from a
+CUDA graph (``include/gbblas.h``, batched API), and ``Engine`` drives the
+serving engine of ``include/gbserve.h`` (continuous batching under an HBM
+budget, resident operand pools, row chunks).
 
 The library must be built (``__graft_entry__.build()`` or
 ``python paper_2108_02025_gb300/build.py``); importing this package without
