@@ -152,3 +152,36 @@ def test_no_cpu_fallback_when_library_missing(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
                        timeout=120)
     assert "refused" in r.stdout, (r.stdout, r.stderr)
+
+
+def test_headers_are_plain_c_and_link_from_c(tmp_path):
+    """include/gbblas.h and include/gbserve.h compile as C99 with every
+    warning an error, and a C program links against libgbblas.so and calls
+    host-only entry points (no device is touched)."""
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text(textwrap.dedent("""
+        #include <stdio.h>
+        #include "gbblas.h"
+        #include "gbserve.h"
+        int main(void) {
+          gb_request r = {0};
+          r.op = GB_REQ_GEMV; r.m = 10; r.n = 10;
+          printf("%d %zu %zu %s\\n", gb_version() > 0,
+                 gb_workspace_bytes(GB_OP_GEMV, GB_F64, GB_ROW_MAJOR, -1, 5),
+                 gb_engine_request_bytes(&r), gb_status_string(GB_ERR_WORKSPACE) != 0 ? "ok" : "no");
+          return 0;
+        }
+    """))
+    inc = os.path.join(ROOT, "include")
+    libdir = os.path.dirname(gb.LIB_PATH)
+    exe = tmp_path / "use"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", inc, str(src), "-o", str(exe),
+                        "-L", libdir, "-lgbblas", f"-Wl,-rpath,{libdir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.split() == ["1", "0", "1024", "ok"]
