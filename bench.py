@@ -1085,6 +1085,151 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------- one-case mode --
+
+def fit_fixed_cost(points):
+    """Least-squares fit of t = t0 + bytes / bw over (bytes, seconds) points:
+    returns (t0 in seconds, bw in bytes per second)."""
+    k = len(points)
+    sx = sum(b for b, _ in points)
+    sy = sum(t for _, t in points)
+    sxx = sum(b * b for b, _ in points)
+    sxy = sum(b * t for b, t in points)
+    den = k * sxx - sx * sx
+    if k < 2 or den == 0:
+        return None, None
+    slope = (k * sxy - sx * sy) / den
+    t0 = (sy - slope * sx) / k
+    return t0, (1.0 / slope if slope > 0 else None)
+
+
+def case_bytes(op, dtype, m, n):
+    """Compulsory bytes of one call of a --case operation."""
+    if op in ("gemv", "dot", "ger"):
+        return alg_bytes(op, dtype, m, n)
+    return precision_bytes(dtype, m, n)
+
+
+def run_case(args):
+    """One operation of the library timed on its own (--case OP DTYPE LAYOUT
+    M N): inputs uniform[-1,1] from the generator (gemvq: the precision
+    workload's A, quantised before timing; batch: M GEMVs of the batched
+    workload in one launch with the tuned table).  Each rep is --batch calls
+    back to back between two CUDA events on the launching stream (the
+    events' resolution is about 2 us), after an L2 flush by a read of 512
+    MB; the calls take copies of the operands in turn (at least 600 MB
+    together), so that none finds its operands in L2.  With
+    --scale k1,k2,... the long dimension (the larger of M and N; n for DOT)
+    is multiplied by each factor in turn and t = t0 + bytes/bw is fitted
+    over the median times, which separates a fixed cost per call from the
+    streaming bandwidth."""
+    import torch
+    import paper_2108_02025_gb300 as gb
+    import synth
+    op, dtype, layout, m0, n0 = args.case
+    m0, n0 = int(m0), int(n0)
+    device = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(device)
+    # L2 flush by reading a buffer of 4x the L2: a write would leave dirty
+    # lines whose write-back overlaps the timed call
+    flush = torch.ones(128 << 20, dtype=torch.float32, device=device)
+    lay = gb.COL_MAJOR if layout == "col" else gb.ROW_MAJOR
+    hbm, src = peaks()
+    scales = [int(s) for s in args.scale.split(",")] if args.scale else [1]
+    rows = []
+    for k in scales:
+        m, n = (m0 * k, n0) if (m0 > n0 and op != "dot") or op == "batch" else (m0, n0 * k)
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+
+        def filled(numel, s):
+            t = torch.empty(max(numel, 1), dtype=tdt, device=device)
+            synth.fill_uniform(t, 0, s)
+            return t
+
+        nb = case_bytes(op, dtype, m, n) if op != "batch" else None
+        # copies of the operands, used in turn, so that no call finds its
+        # operands in L2 (together at least 4.5x the L2)
+        copies = 1 if op == "batch" else max(1, min(8, -(-(600 << 20) // nb)))
+        calls = []
+        for r in range(copies):
+            if op == "gemv":
+                A, x, c = filled(m * n, 1 + 10 * r), filled(n, 2 + 10 * r), filled(m, 3 + 10 * r)
+                ld = n if lay == gb.ROW_MAJOR else m
+                calls.append(lambda A=A, x=x, c=c, ld=ld: gb.gemv(A, x, c, 1.0, lay, m, n, ld))
+            elif op == "dot":
+                x, y, a = filled(n, 4 + 10 * r), filled(n, 5 + 10 * r), filled(1, 6 + 10 * r)
+                calls.append(lambda x=x, y=y, a=a: gb.dot(x, y, a, n))
+            elif op == "ger":
+                C, x, y = filled(m * n, 7 + 10 * r), filled(m, 8 + 10 * r), filled(n, 9 + 10 * r)
+                ld = n if lay == gb.ROW_MAJOR else m
+                calls.append(lambda C=C, x=x, y=y, ld=ld: gb.ger(x, y, C, 1.0, lay, m, n, ld))
+            elif op == "batch":  # M FP32 GEMVs of the batched workload in one launch; N unused
+                bw_ = BatchWorkload(device, count=m)
+                b = gb.Batch(bw_.problems, table=gb.load_tuning())
+                nb = bw_.bytes
+                calls.append(lambda b=b: b.launch())
+            else:  # gemvq: dtype bf16 or e4m3
+                A = torch.empty((m, n), dtype=torch.float32, device=device)
+                synth.fill_normal_rows(A, 0, 1, -3.0, 3.0)
+                x, c = filled(n, 2 + 10 * r), filled(m, 3 + 10 * r)
+                Q, sc = gb.quantize(A, dtype)
+                del A
+                calls.append(lambda Q=Q, sc=sc, x=x, c=c: gb.gemv_q(Q, sc, x, c, 1.0, n=n))
+        for i in range(3 * copies):
+            calls[i % copies]()
+        torch.cuda.synchronize(device)
+        times = []
+        for _ in range(args.reps):
+            flush.sum()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(args.batch):
+                calls[i % copies]()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3 / args.batch)
+        times.sort()
+        med = times[len(times) // 2]
+        rows.append({"scale": k, "m": m, "n": n, "bytes": nb, "copies": copies,
+                     "us_median": round(med * 1e6, 2), "us_min": round(times[0] * 1e6, 2),
+                     "GB_s": round(nb / med / 1e9, 1), "frac_hbm": round(nb / med / 1e9 / hbm, 4)})
+        del calls
+        torch.cuda.empty_cache()
+    out = {"case": [op, dtype, layout, m0, n0], "reps": args.reps, "calls_per_rep": args.batch,
+           "l2": "flushed (512 MB read) before each rep; the calls of a rep take the operand copies in turn",
+           "peak_gbs": hbm, "peak_source": src, "points": rows}
+    if len(rows) >= 2:
+        t0, bw = fit_fixed_cost([(r["bytes"], r["us_median"] * 1e-6) for r in rows])
+        out["fit"] = {"t0_us": round(t0 * 1e6, 2) if t0 is not None else None,
+                      "bw_GB_s": round(bw / 1e9, 1) if bw else None,
+                      "bw_frac_hbm": round(bw / 1e9 / hbm, 4) if bw else None}
+    print(json.dumps(out), flush=True)
+
+
+def run_serve_case(args):
+    """One seeded Poisson stream through the serving engine alone (--serve):
+    the serving workload (70% GEMV / 20% DOT / 10% GER, m and n log-uniform
+    in [32, 16384], 4 streams) on resident operand pools of
+    2^pool_log2 FP32 and BF16 values (or every operand drawn per request,
+    --serve-drawn), under an HBM budget of --serve-budget-gb GB.  With the
+    default rate every request arrives at once, which measures capacity; with
+    --serve-loads the stream is served at saturation and then, the same
+    requests, at 50%, 80% and 95% of the measured rate.  A small budget and
+    pool keep the device footprint small enough for a profiler capture."""
+    import paper_2108_02025_gb300 as gb
+    form = gb.FORM_BF16 if args.serve_bf16 else gb.FORM_F32
+    chunk = SERVE_CHUNK if args.serve_chunk_mb is None else int(args.serve_chunk_mb * (1 << 20))
+    if args.serve_loads:
+        r = serve_loads(args.serve, form, seed=args.serve_seed, chunk_bytes=chunk, pool=not args.serve_drawn)
+        r = {"chunk_bytes": chunk, "saturated": r["saturated"]["solves_per_s"],
+             "loads": {f: (v["solves_per_s"], v["p50_us"], v["p99_us"]) for f, v in r["loads"].items()}}
+    else:
+        r = serve_once(args.serve, args.serve_rate, form, seed=args.serve_seed, sample=0,
+                       pool=not args.serve_drawn, budget=int(args.serve_budget_gb * (1 << 30)),
+                       pool_elems=1 << args.serve_pool_log2, chunk_bytes=chunk)
+    print(json.dumps(r), flush=True)
+
+
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     p.add_argument("--gpus", type=int, default=1)
@@ -1096,7 +1241,33 @@ def main(argv=None):
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     p.add_argument("--no-growth", action="store_true",
                    help="skip the reduced-precision, batched and serving legs")
+    p.add_argument("--case", nargs=5, metavar=("OP", "DTYPE", "LAYOUT", "M", "N"),
+                   help="time one operation alone: OP gemv|dot|ger|gemvq|batch, DTYPE f32|f64|bf16|e4m3, "
+                        "LAYOUT row|col|-; for batch, M is the number of GEMVs")
+    p.add_argument("--scale", default=None,
+                   help="with --case: factors of the long dimension, e.g. 1,2,4,8, and a fit t = t0 + bytes/bw")
+    p.add_argument("--reps", type=int, default=20, help="with --case: timed reps per size")
+    p.add_argument("--batch", type=int, default=20, help="with --case: calls per rep, back to back")
+    p.add_argument("--serve", type=int, default=None, metavar="REQUESTS",
+                   help="serve one stream of this many requests through the engine alone")
+    p.add_argument("--serve-rate", type=float, default=1e7, help="with --serve: arrivals per second")
+    p.add_argument("--serve-bf16", action="store_true", help="with --serve: A stored as BF16")
+    p.add_argument("--serve-seed", type=int, default=1)
+    p.add_argument("--serve-drawn", action="store_true", help="with --serve: operands drawn per request, no pool")
+    p.add_argument("--serve-budget-gb", type=float, default=64.0)
+    p.add_argument("--serve-pool-log2", type=int, default=30)
+    p.add_argument("--serve-chunk-mb", type=float, default=None,
+                   help="with --serve: row chunk size in MB (default: the benchmark's; 0: whole requests)")
+    p.add_argument("--serve-loads", action="store_true", help="with --serve: saturation, then 50/80/95%% of it")
     args = p.parse_args(argv)
+    if args.serve is not None:
+        run_serve_case(args)
+        return
+    if args.case:
+        if args.case[0] not in ("gemv", "dot", "ger", "gemvq", "batch"):
+            p.error("--case OP must be gemv, dot, ger, gemvq or batch")
+        run_case(args)
+        return
     if args.warmup < 3 and args.impl == "ours":
         p.error("--warmup must be at least 3")
     if args.impl == "reference":

@@ -327,25 +327,32 @@ int gb_batch_plan(int64_t count, const gb_batch_item *items, const gb_batch_tuni
                   size_t plan_bytes);
 
 /* GEMV without allocation.  The paper has no counterpart: this entry point
-   exists for callers that cannot allocate device memory (code running where
-   cudaMalloc is not allowed, such as a host callback, or a runtime that owns
-   the whole device heap) and so cannot pass the workspace of gb_dgemv.
+   exists for callers that cannot allocate device memory (a runtime that owns
+   the whole device heap, or code that must not allocate once it is set up)
+   and so cannot pass the workspace of gb_dgemv.
    It computes exactly what gb_dgemv computes, with the same kernels, but its
    split sums use a scratch array of GB_NOALLOC_SCRATCH_BYTES compiled into
    the library, which every GPU that loads the library holds until the
    process exits.  It calls no cudaMalloc, cudaFree or other allocating
-   routine.
+   routine.  Like every call here it uses the CUDA runtime, so it must not be
+   called from a host callback or stream callback (cudaLaunchHostFunc),
+   where CUDA calls are not allowed.
      Arguments 1-8 as for gb_dgemv; stream is argument 9.
      Returns what gb_dgemv returns, and GB_ERR_WORKSPACE (nothing enqueued)
      when the call would need more than GB_NOALLOC_SCRATCH_BYTES of scratch,
      that is when gb_workspace_bytes(GB_OP_GEMV, GB_F64, layout, m, n)
-     exceeds it.
+     exceeds it.  A call refused for any reason (invalid argument, too large,
+     GB_FAULT_INJECT) enqueues nothing.
    The first call on a device looks up the array's device address with that
-   device current (cudaGetSymbolAddress); make that first call before any
-   stream capture.  Each call first zeroes the array's counters on `stream`
-   (cudaMemsetAsync), because the array keeps the previous call's contents.
-   All calls share the one array: calls that overlap on the GPU (different
-   streams, different threads) race and give wrong results; serialise them. */
+   device current (cudaGetSymbolAddress), and looks it up again when the
+   device's context has changed (after cudaDeviceReset); make that first call
+   before any stream capture.  A call that uses the array first zeroes its
+   counters on `stream` (cudaMemsetAsync): the kernels return them to zero
+   as they finish, but a call that did not run to the end, or that
+   overlapped another, can leave them set, and the array otherwise keeps the
+   previous call's contents.  All calls share the one array: calls that
+   overlap on the GPU (different streams, different threads) race and give
+   wrong results; serialise them. */
 #define GB_NOALLOC_SCRATCH_BYTES ((size_t)256 << 10)  /* 256 KiB */
 int gb_dgemv_noalloc(int layout, int64_t m, int64_t n, double alpha, const double *A,
                      int64_t lda, const double *x, double *c, gb_stream stream);

@@ -2,6 +2,7 @@
 // work plans, workspace layout and kernel dispatch.  Host code only; nothing
 // here allocates, frees or synchronises.
 #include <atomic>
+#include <cuda.h>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -359,9 +360,17 @@ inline int cuda_status() {
 
 // ------------------------------------------------------------- dispatch ---
 
-template <typename T>
+// No work between the checks and the launch (gb_dgemv, gb_sgemv).
+struct NoPrelaunch {
+  int operator()() const { return GB_OK; }
+};
+
+// `pre` runs after every argument check and the fault-injection check,
+// immediately before the launch; a status other than GB_OK from it is
+// returned with nothing launched.
+template <typename T, typename Pre = NoPrelaunch>
 int gemv(int layout, int64_t m, int64_t n, T alpha, const T* A, int64_t lda, const T* x, T* c,
-         void* ws, size_t ws_bytes, gb_stream stream) {
+         void* ws, size_t ws_bytes, gb_stream stream, Pre pre = Pre{}) {
   if (layout != GB_ROW_MAJOR && layout != GB_COL_MAJOR) return -1;
   if (m < 0) return -2;
   if (n < 0) return -3;
@@ -379,6 +388,7 @@ int gemv(int layout, int64_t m, int64_t n, T alpha, const T* A, int64_t lda, con
   if (need > 0 && (!ws || !aligned16(ws))) return -9;
   if (ws_bytes < need) return GB_ERR_WORKSPACE;
   if (injected(GB_OP_GEMV)) return GB_ERR_INJECTED;
+  if (const int st = pre(); st != GB_OK) return st;
 
   const int64_t V = 16 / (int64_t)e;
   const bool vec = aligned16(A) && aligned16(x) && lda % V == 0;
@@ -498,7 +508,7 @@ int qgemv(int fmt, int64_t m, int64_t n, float alpha, const void* Q, int64_t ldq
 bool fault_injected(int site) { return injected(site); }
 
 // Occupancy of each kernel is queried once per (kernel, device).
-int grid_size(const void* kernel, int64_t units, size_t smem) {
+int grid_size(const void* kernel, int64_t units, size_t smem, int waves) {
   struct Entry {
     const void* k;
     int dev;
@@ -522,7 +532,8 @@ int grid_size(const void* kernel, int64_t units, size_t smem) {
       if (used < 256) cache[used++] = Entry{kernel, dev, blocks};
     }
   }
-  return (int)(units < blocks ? (units > 0 ? units : 1) : blocks);
+  const int64_t want = (int64_t)blocks * (waves > 1 ? waves : 1);
+  return (int)(units < want ? (units > 0 ? units : 1) : want);
 }
 
 bool allow_smem(const void* kernel, size_t bytes) {
@@ -675,10 +686,12 @@ int gb_gemv_e4m3(int64_t m, int64_t n, float alpha, const uint8_t* Q, int64_t ld
 // ------------------------------------------------- GEMV without allocation ---
 //
 // gb_dgemv_noalloc: the FP64 GEMV of gb_dgemv for callers that cannot call
-// cudaMalloc or take memory from an allocator (code inside a host callback
-// or a custom runtime that owns the device heap, for example).  Its split
-// sums use a scratch array compiled into this library instead of a
-// caller-supplied workspace.
+// cudaMalloc or take memory from an allocator (a runtime that owns the whole
+// device heap, or code that must not allocate once set up, for example).
+// Its split sums use a scratch array compiled into this library instead of a
+// caller-supplied workspace.  Like every entry point here it calls the CUDA
+// runtime, so it must not be called from a host callback or stream callback
+// (cudaLaunchHostFunc), where CUDA calls are not allowed.
 
 namespace gb {
 namespace {
@@ -691,20 +704,51 @@ constexpr int kNoAllocMaxDevices = 64;
 // cudaGetSymbolAddress (noalloc_scratch below).
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current) and cached; nullptr on failure.
+// Identity of the calling thread's current context (0 when it cannot be
+// told), through the driver entry points the runtime hands out, so that a
+// context rebuilt after cudaDeviceReset is seen as a new one.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array in the current context, looked up
+// with cudaGetSymbolAddress the first time a context of a device calls, and
+// again whenever the device's context has changed since (cudaDeviceReset
+// rebuilds it, and the array with it); nullptr on failure.
 void* noalloc_scratch() {
   static std::mutex mu;
   static void* addr[kNoAllocMaxDevices] = {};
+  static unsigned long long ctx_of[kNoAllocMaxDevices] = {};
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return nullptr;
   std::lock_guard<std::mutex> lock(mu);
-  if (addr[dev] == nullptr) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return nullptr;
-    addr[dev] = p;
-  }
-  return addr[dev];
+  const unsigned long long ctx = current_context_id();
+  if (addr[dev] != nullptr && ctx != 0 && ctx == ctx_of[dev]) return addr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return nullptr;
+  addr[dev] = p;
+  ctx_of[dev] = current_context_id();  // the lookup made the context current if none was
+  return p;
 }
 
 // Bytes at the start of the workspace that hold arrival counters (they must
@@ -726,26 +770,27 @@ size_t noalloc_ticket_bytes(int layout, int64_t m, int64_t n) {
 extern "C" int gb_dgemv_noalloc(int layout, int64_t m, int64_t n, double alpha, const double* A,
                                 int64_t lda, const double* x, double* c, gb_stream stream) {
   using namespace gb;
-  // Argument checks in the order of gb_dgemv, so that an invalid call
-  // returns the same status and enqueues nothing.
-  const bool shape_ok = (layout == GB_ROW_MAJOR || layout == GB_COL_MAJOR) && m >= 0 && n >= 0 &&
-                        lda >= (layout == GB_ROW_MAJOR ? (n > 1 ? n : 1) : (m > 1 ? m : 1));
-  if (!shape_ok || m == 0 || n == 0 || alpha == 0.0 || !A || !x || !c)
+  const bool shape_ok = (layout == GB_ROW_MAJOR || layout == GB_COL_MAJOR) && m >= 0 && n >= 0;
+  const size_t need = shape_ok && m > 0 && n > 0 ? gemv_ws(sizeof(double), layout, m, n) : 0;
+  if (need == 0)  // no split sums: gb_dgemv itself, which needs no workspace here
     return gemv<double>(layout, m, n, alpha, A, lda, x, c, nullptr, 0, stream);
-  const unsigned __int128 cb = (unsigned __int128)m * sizeof(double);
-  if (overlap(c, cb, A, matrix_bytes(layout, m, n, lda, sizeof(double))) ||
-      overlap(c, cb, x, (unsigned __int128)n * sizeof(double)))
-    return -8;
-  const size_t need = gemv_ws(sizeof(double), layout, m, n);
-  if (need > kNoAllocScratchBytes) return GB_ERR_WORKSPACE;  // the built-in scratch is too small
-  void* ws = nullptr;
-  if (need > 0) {
-    ws = noalloc_scratch();
-    if (ws == nullptr) return GB_ERR_CUDA;
-    // The array keeps the previous call's contents: zero the counters.
-    const size_t tb = noalloc_ticket_bytes(layout, m, n);
+  if (need > kNoAllocScratchBytes) {
+    // the built-in scratch is too small: gb_dgemv's checks without a
+    // workspace give an invalid argument's own status first, else -9 (the
+    // missing workspace), reported as GB_ERR_WORKSPACE; nothing is launched
+    const int st = gemv<double>(layout, m, n, alpha, A, lda, x, c, nullptr, 0, stream);
+    return st == -9 ? GB_ERR_WORKSPACE : st;
+  }
+  void* ws = noalloc_scratch();
+  if (ws == nullptr) return GB_ERR_CUDA;
+  // Once every check has passed (so that a refused or injected call enqueues
+  // nothing): zero the counters.  The kernels return them to zero as they
+  // finish, so this only matters after a call that did not run to the end or
+  // overlapped another one; the array otherwise keeps the last call's data.
+  const size_t tb = noalloc_ticket_bytes(layout, m, n);
+  return gemv<double>(layout, m, n, alpha, A, lda, x, c, ws, need, stream, [&] {
     if (tb > 0 && cudaMemsetAsync(ws, 0, tb, static_cast<cudaStream_t>(stream)) != cudaSuccess)
       return GB_ERR_CUDA;
-  }
-  return gemv<double>(layout, m, n, alpha, A, lda, x, c, ws, need, stream);
+    return GB_OK;
+  });
 }

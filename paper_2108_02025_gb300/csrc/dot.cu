@@ -23,7 +23,8 @@ namespace gb {
 namespace {
 
 constexpr int kDotEmu64 = 2;  // FP64: packs per step (of 4) formed on the FP32 pipe
-constexpr int kDotEmuFlush = kDotEmu64 > 0 ? 16 / kDotEmu64 : 1;  // steps per FP32 pair: <= 32 products
+// steps per FP32 pair: kDotEmu64 packs of 2 products each, at most kEmuChain products
+constexpr int kDotEmuFlush = kDotEmu64 > 0 && kEmuChain / (2 * kDotEmu64) > 0 ? kEmuChain / (2 * kDotEmu64) : 1;
 
 // Per-thread accumulator of the sum of products.
 template <typename T>
@@ -114,8 +115,7 @@ __global__ void __launch_bounds__(kThreads, 4)
           }
         if (++ebody == kDotEmuFlush) {
           ebody = 0;
-          acc.a3 = __dadd_rn(acc.a3, __dadd_rn((double)eh, (double)el));
-          eh = el = 0.f;
+          emu_fold(acc.a3, eh, el);
         }
       } else {
         DPacks<kDotEmu64 * V> dp;
@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(kThreads, 4)
   }
   for (int64_t k = hv + threadIdx.x; k < hi; k += kThreads) acc.add(__ldcs(x + k), __ldcs(y + k), 0);
 
-  const double bsum = block_sum(__dadd_rn(acc.total(), __dadd_rn((double)eh, (double)el)), red);
+  if constexpr (sizeof(T) == 8) emu_fold(acc.a3, eh, el);
+  const double bsum = block_sum(acc.total(), red);
 
   if (gridDim.x == 1) {  // one block: Alg. 3, no workspace
     if (threadIdx.x == 0) *alpha = (T)__dadd_rn((double)*alpha, bsum);

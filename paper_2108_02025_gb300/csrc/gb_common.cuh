@@ -142,6 +142,34 @@ __device__ __forceinline__ void emu_fma(float ah, float al, float xh, float xl, 
   L = __fadd_rn(L, __fadd_rn(err, t));
 }
 
+// At most this many emulated products enter one FP32 pair before it is
+// folded into an FP64 sum (emu_fold).  With K products per pair, the pair's
+// rounding errors are at most u^2 (K(K+1)/2 - 1) + u (K+1) 1.25*2^-22 of the
+// sum of |a x| of its products (u = 2^-24); with the 2.5*2^-45 per product
+// of the operand cuts and of t, a chain of 16 is within 8.6e-13 of it.
+constexpr int kEmuChain = 16;
+
+// FP64 value of an FP32 pair word by integer operations (no FP64
+// instruction: the small FP64 pipe is the limit of the FP64 kernels); exact
+// for zero and normal numbers.  A subnormal word (below 2^-126, reachable
+// only by cancellation inside a cross term) is taken as zero: an error below
+// 2^-126 beside a sum of |a x| of at least 2^-60 (both operands pass emu_ok).
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sgn = b & 0x80000000u;
+  const bool nz = (b & 0x7F800000u) != 0u;
+  const unsigned hi = nz ? (((b & 0x7FFFFFFFu) >> 3) + (896u << 20)) | sgn : sgn;
+  const unsigned lo = nz ? b << 29 : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// acc <- acc + (H + L) with two FP64 additions, the pair reset to zero.
+__device__ __forceinline__ void emu_fold(double& acc, float& H, float& L) {
+  acc = __dadd_rn(acc, __dadd_rn(f2d_exact(H), f2d_exact(L)));
+  H = 0.f;
+  L = 0.f;
+}
+
 // The FP64 fallback of a group of emulated packs (an operand out of range):
 // kept out of line, so that the hot path holds no FP64 instruction even when
 // the compiler predicates the branch around the call.

@@ -32,14 +32,15 @@ constexpr int kRowLongB64 = 4;   // FP64 long-row kernel: resident blocks per SM
 // resident blocks per SM.
 constexpr int kRowMultiR = 2;
 constexpr int kRowMultiU = 4;
-constexpr int kRowMultiD = 1;
-constexpr int kRowMultiB = 3;
+constexpr int kRowMultiD = 2;
+constexpr int kRowMultiB = 4;
 constexpr int kRowMultiMinRows = 16;  // fewer FP64 rows take the one-row long kernel
 constexpr int kRowShortD64 = 2;  // FP64 short rows: of a lane's 8 packs, those on the FP64 pipe
 constexpr int kRowShortB64 = 4;  // FP64 short rows: resident blocks per SM budgeted for
 constexpr int64_t kRowShortPPL = 8;  // short rows: packs per lane the lanes per row are sized for (<= 8)
 constexpr int kRowScalarRW = 4;  // rows per lane group, misaligned row-major kernel
 constexpr int kColTileU = 8;     // columns in flight per thread, column-major tile kernel
+constexpr int kColTileD64 = 4;   // FP64: of those, columns formed on the FP64 pipe (the rest emulated)
 constexpr int64_t kColShortN = 512;  // column-major: n up to this takes tiles of up to 256 row threads
 constexpr int64_t kColMinUnits = 1;  // column-major: split until at least this many units per block
 constexpr int64_t kRowMinUnits = 2;  // row-major long rows: the same
@@ -98,9 +99,16 @@ struct GerPlan {
   int64_t lines, len;
 };
 
-// Blocks to launch for `units` independent work units: every SM filled to
-// the kernel's occupancy, never more blocks than units.
-int grid_size(const void* kernel, int64_t units, size_t smem = 0);
+// Blocks to launch for `units` independent work units: `waves` times the
+// blocks that fit on the GPU at once (every SM filled to the kernel's
+// occupancy), never more blocks than units.  With waves > 1 a block that
+// finishes early is replaced by the next one, which evens out the end of
+// the launch when blocks stream at different rates.
+int grid_size(const void* kernel, int64_t units, size_t smem = 0, int waves = 1);
+// Waves of the FP64 kernels (measured on GB300): the row-group kernel and
+// the column tile kernel with FP64 products.
+constexpr int kRowMultiWaves = 8;
+constexpr int kColTileWaves64 = 4;
 
 // Batched level-2 problems (batch.cu): gb_batch_item kinds, and the
 // planner behind gb_sgemv_batch_plan / gb_batch_plan with the statuses of

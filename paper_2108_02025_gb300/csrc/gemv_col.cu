@@ -146,9 +146,10 @@ __global__ void __launch_bounds__(kThreads, 3)
 // 16-byte aligned operands: block tiles.  A work unit is a tile of RT = TX*V
 // rows by a chunk of KC columns; thread (tx, ty) owns rows tx*V .. tx*V+V-1
 // of the tile (one 16-byte pack per column) and every TY-th column of the
-// chunk, with U packs in flight.  Block b takes the consecutive units
-// [b*units/G, (b+1)*units/G), so the blocks divide the work evenly and each
-// reads long runs of consecutive columns.  The TY partial vectors are summed
+// chunk, with U packs in flight.  Block b takes the units b, b + G,
+// b + 2G, ... (G blocks), so that at any moment the blocks read one compact
+// window of memory that moves through A (measured on GB300: a higher
+// stream rate and a shorter start than a contiguous range per block).  The TY partial vectors are summed
 // through shared memory in ty order; S > 1 chunk partials are combined by
 // block_split_finish.  FP32 sums stay in FP32 (chains of at most 64
 // products, then a compensated FP32 sum).
@@ -160,7 +161,8 @@ __global__ void __launch_bounds__(kThreads, 4)
   constexpr int TY = kThreads / TX;
   constexpr int RT = TX * V;  // rows per tile
   constexpr int FLUSH = LONG ? (64 / U > 0 ? 64 / U : 1) : 1 << 30;
-  constexpr int EFLUSH = 32 / (U - U / 2) > 0 ? 32 / (U - U / 2) : 1;
+  constexpr int DU = sizeof(T) == 8 ? kColTileD64 : U;  // FP64: columns on the FP64 pipe per iteration
+  constexpr int EFLUSH = U > DU && kEmuChain / (U - DU) > 0 ? kEmuChain / (U - DU) : 1;
   __shared__ T redT[kThreads * V];
   __shared__ double red_d[kThreads];
   __shared__ int flag;
@@ -168,11 +170,9 @@ __global__ void __launch_bounds__(kThreads, 4)
   const int tx = threadIdx.x % TX;
   const int ty = threadIdx.x / TX;
   const int S = sp.S;
-  const int64_t u0 = units * blockIdx.x / gridDim.x;
-  const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
   const int64_t cstep = (int64_t)TY * lda;  // between a thread's columns
 
-  for (int64_t u = u0; u < u1; ++u) {
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {  // interleaved units
     const int64_t rt = u / S;
     const int s = (int)(u - rt * S);
     const int64_t i0 = rt * RT + (int64_t)tx * V;
@@ -200,15 +200,15 @@ __global__ void __launch_bounds__(kThreads, 4)
         }
         pa += U * cstep;
         if constexpr (sizeof(T) == 8) {
-          // FP64: the first half of the columns on the FP64 pipe, the second
-          // half with FP32 instructions (emu_fma) into the pairs (eh, el)
+          // FP64: the first DU columns on the FP64 pipe, the others with
+          // FP32 instructions (emu_fma) into the pairs (eh, el)
 #pragma unroll
-          for (int q = 0; q < U / 2; ++q)
+          for (int q = 0; q < DU; ++q)
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = fma_rn(ap[q].v[v], xs[q], acc[v]);
           bool ok = true;
 #pragma unroll
-          for (int q = U / 2; q < U; ++q) {
+          for (int q = DU; q < U; ++q) {
             ok = ok && emu_ok(xs[q]);
 #pragma unroll
             for (int v = 0; v < V; ++v) ok = ok && emu_ok(ap[q].v[v]);
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 4)
           // predicated-off one would still occupy the FP64 pipe)
           if (__all_sync(__activemask(), ok)) {
 #pragma unroll
-            for (int q = U / 2; q < U; ++q) {
+            for (int q = DU; q < U; ++q) {
               float xh, xl;
               emu_split(xs[q], xh, xl);
 #pragma unroll
@@ -232,23 +232,19 @@ __global__ void __launch_bounds__(kThreads, 4)
           } else {
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-              DPacks<U - U / 2> dp;
+              DPacks<U - DU> dp;
 #pragma unroll
-              for (int q = U / 2; q < U; ++q) {
-                dp.a[q - U / 2] = ap[q].v[v];
-                dp.x[q - U / 2] = xs[q];
+              for (int q = DU; q < U; ++q) {
+                dp.a[q - DU] = ap[q].v[v];
+                dp.x[q - DU] = xs[q];
               }
               acc[v] = dfma_fallback(dp, acc[v]);
             }
           }
-          if (++ebody == EFLUSH) {  // at most 32 products per row in the FP32 pairs
+          if (++ebody == EFLUSH) {  // at most kEmuChain products per row in the FP32 pairs
             ebody = 0;
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-              acc[v] = __dadd_rn(acc[v], __dadd_rn((double)eh[v], (double)el[v]));
-              eh[v] = 0.f;
-              el[v] = 0.f;
-            }
+            for (int v = 0; v < V; ++v) emu_fold(acc[v], eh[v], el[v]);
           }
         } else {
 #pragma unroll
@@ -303,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 4)
     }
     if constexpr (sizeof(T) == 8) {
 #pragma unroll
-      for (int v = 0; v < V; ++v) acc[v] = __dadd_rn(acc[v], __dadd_rn((double)eh[v], (double)el[v]));
+      for (int v = 0; v < V; ++v) emu_fold(acc[v], eh[v], el[v]);
     }
 
     __syncthreads();  // redT is free
@@ -329,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 4)
 template <typename T, int V, int TX, bool LONG>
 int launch_tile(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
   auto kern = gemv_col_tile_kernel<T, V, TX, kColTileU, LONG>;
-  const int grid = grid_size((const void*)kern, p.units);
+  const int grid = grid_size((const void*)kern, p.units, 0, sizeof(T) == 8 ? kColTileWaves64 : 1);
   kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c, p.split, p.kc, p.units);
   return 0;
 }

@@ -7,8 +7,10 @@
 // * long rows (more than 256 16-byte packs): a work unit is one chunk of KC
 //   columns of one row (KC = n unless the rows are too few to fill the GPU,
 //   when the columns are split into S chunks, the blocking of the index
-//   range of Alg. 4).  Block b takes the consecutive units
-//   [b*units/G, (b+1)*units/G) and streams each with all 256 threads
+//   range of Alg. 4).  Block b takes the units b, b + G, b + 2G, ... (G
+//   blocks: the blocks read one compact window that moves through A, which
+//   streams faster on GB300 than a contiguous range per block) and streams
+//   each with all 256 threads
 //   (16-byte loads, U packs per thread in flight), then sums the unit in a
 //   fixed order (warp butterfly, then warps in order).  A split row's chunk
 //   partials are summed in chunk order by the block that finishes the row.
@@ -61,15 +63,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowLongB64 : 4)
   // FLUSH bodies it is folded into a compensated FP32 sum (TwoSum)
   constexpr int FLUSH = LONG ? (64 / (U * V) > 0 ? 64 / (U * V) : 1) : 1 << 30;
   constexpr int UD = sizeof(T) == 8 ? (kRowLongD64 < U ? kRowLongD64 : U) : U;  // packs on the FP64 pipe
-  constexpr int EFLUSH = (U - UD) * V > 0 && 32 / ((U - UD) * V) > 0 ? 32 / ((U - UD) * V) : 1;
+  constexpr int EFLUSH = (U - UD) * V > 0 && kEmuChain / ((U - UD) * V) > 0 ? kEmuChain / ((U - UD) * V) : 1;
   __shared__ double red_d[kThreads / 32];
   __shared__ int flag;
   T* red = reinterpret_cast<T*>(red_d);
 
   const int S = sp.S;
-  const int64_t u0 = units * blockIdx.x / gridDim.x;
-  const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
-  for (int64_t u = u0; u < u1; ++u) {
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {  // interleaved units
     const int64_t row = u / S;
     const int s = (int)(u - row * S);
     const int64_t k0 = (int64_t)s * KC;
@@ -130,11 +130,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowLongB64 : 4)
             }
           acc = dfma_fallback(dp, acc);
         }
-        if (++body == EFLUSH) {  // at most 32 products in the FP32 pair
+        if (++body == EFLUSH) {  // at most kEmuChain products in the FP32 pair
           body = 0;
-          acc = __dadd_rn(acc, __dadd_rn((double)eh, (double)el));
-          eh = 0.f;
-          el = 0.f;
+          emu_fold(acc, eh, el);
         }
       } else {
 #pragma unroll
@@ -165,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowLongB64 : 4)
     if constexpr (LONG) acc = hi + (lo + acc);
     if constexpr (sizeof(T) == 8) {
       acc = __dadd_rn(acc, acc2);
-      acc = __dadd_rn(acc, __dadd_rn((double)eh, (double)el));
+      emu_fold(acc, eh, el);
     }
 
     const T total = block_total<T>(acc, red);
@@ -285,9 +283,7 @@ __global__ void __launch_bounds__(kThreads, 4)
   __shared__ int flag;
   T* red = reinterpret_cast<T*>(red_d);
   const int S = sp.S;
-  const int64_t u0 = units * blockIdx.x / gridDim.x;
-  const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
-  for (int64_t u = u0; u < u1; ++u) {
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {  // interleaved units
     const int64_t row = u / S;
     const int s = (int)(u - row * S);
     const int64_t k0 = (int64_t)s * KC;  // a multiple of V
@@ -341,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, 4)
 // of the U packs in flight go to the FP64 pipe (two chains), the rest to
 // emu_fma, voted per iteration as in the long-row kernel.  A group's missing
 // rows (past m) re-read row m-1 and are dropped.  Block b takes the units
-// [b*units/G, (b+1)*units/G); with S > 1 chunks the block that finishes a
+// b, b + G, b + 2G, ...; with S > 1 chunks the block that finishes a
 // group sums each row's S partials in chunk order (one counter per group).
 template <int R, int U, int D, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, kRowMultiB)
@@ -351,16 +347,14 @@ __global__ void __launch_bounds__(kThreads, kRowMultiB)
   constexpr int V = 2;
   constexpr int64_t STEP = (int64_t)kThreads * V;
   constexpr int NE = (U - D) * V;  // emulated products per row per iteration
-  constexpr int EFLUSH = NE > 0 && 32 / NE > 0 ? 32 / NE : 1;
+  constexpr int EFLUSH = NE > 0 && kEmuChain / NE > 0 ? kEmuChain / NE : 1;
   static_assert(D < U, "some packs are emulated");
   __shared__ double red[R][kThreads / 32];
   __shared__ int flag;
 
   const int S = SPLIT ? sp.S : 1;
-  const int64_t u0 = units * blockIdx.x / gridDim.x;
-  const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
   const int64_t jlast = (int64_t)(31 - (threadIdx.x & 31)) * V;
-  for (int64_t u = u0; u < u1; ++u) {
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {  // interleaved units
     const int64_t grp = SPLIT ? u / S : u;
     const int s = SPLIT ? (int)(u - grp * S) : 0;
     const int64_t row0 = grp * R;
@@ -432,13 +426,10 @@ __global__ void __launch_bounds__(kThreads, kRowMultiB)
           acc[r] = dfma_fallback(dp, acc[r]);
         }
       }
-      if (++body == EFLUSH) {  // at most 32 products in each FP32 pair
+      if (++body == EFLUSH) {  // at most kEmuChain products in each FP32 pair
         body = 0;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          acc[r] = __dadd_rn(acc[r], __dadd_rn((double)eh[r], (double)el[r]));
-          eh[r] = el[r] = 0.f;
-        }
+        for (int r = 0; r < R; ++r) emu_fold(acc[r], eh[r], el[r]);
       }
     }
 #pragma unroll 1
@@ -462,7 +453,8 @@ __global__ void __launch_bounds__(kThreads, kRowMultiB)
     __syncthreads();  // red is free
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const double v = group_sum<32>(__dadd_rn(__dadd_rn(acc[r], acc2[r]), __dadd_rn((double)eh[r], (double)el[r])));
+      emu_fold(acc[r], eh[r], el[r]);
+      const double v = group_sum<32>(__dadd_rn(acc[r], acc2[r]));
       if ((threadIdx.x & 31) == 0) red[r][threadIdx.x >> 5] = v;
     }
     __syncthreads();
@@ -484,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, kRowMultiB)
 
 // Short rows (S = 1, at most 32*8 packs).  LPR lanes per row, each with up
 // to 8 packs (pack k*LPR + l of the row), so a block iteration reads
-// 256/LPR consecutive rows; block b takes rows [b*m/G, (b+1)*m/G).
+// 256/LPR consecutive rows; block b takes the row blocks b, b + G, ....
 template <typename T, int V, int LPR>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowShortB64 : 4)
     gemv_row_short_kernel(int64_t m, int64_t n, T alpha, const T* __restrict__ A, int64_t lda,
@@ -493,8 +485,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowShortB64 : 4)
   constexpr int PMAX = 8;
   const int l = threadIdx.x % LPR;
   const int g = threadIdx.x / LPR;
-  const int64_t r0 = m * blockIdx.x / gridDim.x;
-  const int64_t r1 = m * (blockIdx.x + 1) / gridDim.x;
   const int64_t packs = n / V;
   const int64_t kv1 = packs * V;
   const bool tail = kv1 + l < n;  // ragged end: lane l takes column kv1 + l
@@ -515,12 +505,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowShortB64 : 4)
   }
 
   // every thread runs the same number of iterations (the butterfly needs
-  // whole warps); rows past r1 are predicated off
+  // whole warps); rows past m are predicated off
 #pragma unroll 1
-  for (int64_t base = r0; base < r1; base += GROUPS) {
+  for (int64_t base = blockIdx.x * (int64_t)GROUPS; base < m; base += (int64_t)gridDim.x * GROUPS) {
     const int64_t row = base + g;
-    const bool ok = row < r1;
-    const T* Ar = A + (ok ? row : r0) * lda;
+    const bool ok = row < m;
+    const T* Ar = A + (ok ? row : base) * lda;
     Pack<T, V> ap[PMAX];
 #pragma unroll
     for (int k = 0; k < PMAX; ++k) {
@@ -546,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowShortB64 : 4)
           for (int v = 0; v < V; ++v) acc = fma_rn(ap[k].v[v], xp.v[v], acc);
         }
       }
-      // packs past the row or of a row past r1 take no part (they add 0)
+      // packs past the row or of a row past m take no part (they add 0)
       bool good = true;
 #pragma unroll
       for (int k = PD; k < PMAX; ++k) {
@@ -571,7 +561,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowShortB64 : 4)
             }
           }
         }
-        acc = __dadd_rn(acc, __dadd_rn((double)eh, (double)el));
+        emu_fold(acc, eh, el);
       } else {
         DPacks<(PMAX - PD) * V> dp;
 #pragma unroll
@@ -632,13 +622,11 @@ __global__ void __launch_bounds__(kThreads, 4)
   constexpr int PMAX = 8;
   const int l = threadIdx.x % LPR;
   const int g = threadIdx.x / LPR;
-  const int64_t r0 = m * blockIdx.x / gridDim.x;
-  const int64_t r1 = m * (blockIdx.x + 1) / gridDim.x;
 #pragma unroll 1
-  for (int64_t base = r0; base < r1; base += GROUPS) {  // the same trips for every thread
+  for (int64_t base = blockIdx.x * (int64_t)GROUPS; base < m; base += (int64_t)gridDim.x * GROUPS) {  // the same trips for every thread
     const int64_t row = base + g;
-    const bool ok = row < r1;
-    const T* Ar = A + (ok ? row : r0) * lda;
+    const bool ok = row < m;
+    const T* Ar = A + (ok ? row : base) * lda;
     const int mis = (int)((reinterpret_cast<uintptr_t>(Ar) / sizeof(T)) % V);
     const T* Ab = Ar - mis;
     const int64_t pv0 = mis > 0 ? 1 : 0;
@@ -731,7 +719,7 @@ int launch_long(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
   if constexpr (sizeof(T) == 8) {
     if (p.multi) {
       auto go = [&](auto kern) {
-        const int grid = grid_size((const void*)kern, p.units);
+        const int grid = grid_size((const void*)kern, p.units, 0, kRowMultiWaves);
         kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c, p.split, p.kc, p.units);
       };
       if (p.split.S > 1) go(gemv_row_multi_f64_kernel<kRowMultiR, kRowMultiU, kRowMultiD, true>);

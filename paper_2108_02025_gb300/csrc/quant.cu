@@ -8,7 +8,7 @@
 //   s_i)); all-zero rows get s_i = 0 and codes 0.
 // * GEMV: c_i <- c_i + alpha * s_i * sum_j q_ij x_j (s_i = 1 for BF16), x
 //   and c FP32.  Row-major only, streamed like the FP32 long-row kernel (a
-//   block per (row group, chunk) unit, consecutive units per block); products
+//   block per (row group, chunk) unit, interleaved units: block b takes b, b + G, ...); products
 //   are FP32 fmas in chains of at most 32, folded into a compensated FP32 sum
 //   (TwoSum), then a fixed-order block sum.
 #include <type_traits>
@@ -118,7 +118,7 @@ __device__ __forceinline__ void unpack4(const uint4& w, int k, float& f0, float&
 }
 
 // Unit u = (row group u / S of R consecutive rows, chunk u % S of the
-// columns); block b takes units [b*U/G, (b+1)*U/G).  Each load of x serves
+// columns); block b takes the units b, b + G, b + 2G, ....  Each load of x serves
 // the R rows of the group: with one byte per element, reading x once per row
 // would cost four times the matrix's own traffic in L1.  A row's products
 // are FP32 fmas in chains of at most 32, folded into a compensated FP32 sum,
@@ -138,9 +138,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
   __shared__ int flag;
 
   const int S = sp.S;
-  const int64_t u0 = units * blockIdx.x / gridDim.x;
-  const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
-  for (int64_t u = u0; u < u1; ++u) {
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {  // interleaved units
     const int64_t g = u / S;
     const int s = (int)(u - g * S);
     const int64_t row0 = g * R;
