@@ -297,9 +297,16 @@ int64_t gb_sgemv_batch_tiles(const void *plan_host);
                          top half of the binary32, decoded exactly)
      GB_BATCH_GER_F32    C <- C + alpha x y^T as fma(x_i, fl(alpha y_j), C_ij)
                          (bit-exact, as gb_sger), C FP32 m x n (lda)
-   Item fields: A = the matrix (GEMV: read; GER: C, read and written);
-   x = the n-vector (GEMV: x; GER: y); c = the m-vector (GEMV: c, read and
-   written; GER: x, read).  Items with m, n or alpha zero are skipped.  The
+     GB_BATCH_DOT_F32    c[0] <- c[0] + A.x (Def. DOT, Sec. 3.1; Algs. 3-4
+                         of Sec. 4.3), A and x FP32 n-vectors, m = 1,
+                         alpha = 1: per-thread compensated products and
+                         sums in FP32 (Dot2), the partials and the initial
+                         c[0] summed in FP64, rounded once to FP32 (as
+                         gb_sdot)
+   Item fields: A = the matrix (GEMV: read; GER: C, read and written; DOT:
+   the first vector); x = the n-vector (GEMV: x; GER: y; DOT: the second
+   vector); c = the m-vector (GEMV: c, read and written; GER: x, read; DOT:
+   the accumulator).  Items with m, n or alpha zero are skipped.  The
    16-byte path needs A and x 16-byte aligned and lda * element bytes a
    multiple of 16; otherwise a scalar path runs in the same launch.  No
    output (GEMV c, GER C) may overlap another output or any input.
@@ -310,7 +317,8 @@ int64_t gb_sgemv_batch_tiles(const void *plan_host);
 typedef enum {
   GB_BATCH_GEMV_F32 = 0,
   GB_BATCH_GEMV_BF16 = 1,
-  GB_BATCH_GER_F32 = 2
+  GB_BATCH_GER_F32 = 2,
+  GB_BATCH_DOT_F32 = 3
 } gb_batch_kind;
 typedef struct {
   int32_t kind;     /* gb_batch_kind */

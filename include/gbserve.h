@@ -22,10 +22,12 @@
  * the operands of requests without GB_REQ_POOL, copies the initial outputs
  * of pool requests and computes their GERs), one persistent launch (the
  * batched kernel of gb_sgemv_batch) for all the step's GEMVs (FP32 or BF16
- * A), DOTs (one-row GEMVs) and the GERs of drawn requests, then the copies
- * of the results to the requests' host buffers and an event.  GEMV and DOT
- * sums are FP32 fma chains of at most 64 products in a compensated FP32
- * sum; GER is one fma per element.  Requests that arrive while steps are
+ * A), DOTs (GB_BATCH_DOT_F32 tiles) and the GERs of drawn requests, then
+ * the copies of the results to the requests' host buffers and an event.
+ * GEMV sums are FP32 fma chains of at most 64 products in a compensated
+ * FP32 sum; a DOT takes compensated FP32 products and sums per thread
+ * (Dot2) and sums the threads' parts and the initial alpha in FP64, rounded
+ * once to FP32, as gb_sdot; GER is one fma per element.  Requests that arrive while steps are
  * on the GPU are admitted and launched in the next step on another stream,
  * so steps overlap on the device.  When a step's event completes, its
  * requests complete (a request in chunks once all its chunks are done),

@@ -218,7 +218,7 @@ class BatchTuning(ctypes.Structure):
 
 
 TuningTable = BatchTuning * BATCH_BUCKETS
-BATCH_GEMV_F32, BATCH_GEMV_BF16, BATCH_GER_F32 = 0, 1, 2
+BATCH_GEMV_F32, BATCH_GEMV_BF16, BATCH_GER_F32, BATCH_DOT_F32 = 0, 1, 2, 3
 
 
 class BatchItem(ctypes.Structure):

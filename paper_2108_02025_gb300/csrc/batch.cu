@@ -375,6 +375,56 @@ __device__ __forceinline__ void row_ger(const BatchTile& tl, int r, int lane, in
   }
 }
 
+// One step of the compensated dot product Dot2 (Ogita, Rump & Oishi, 2005)
+// in FP32: (p, s) <- p + s + a*b with the product split exactly by an fma
+// (TwoProduct) and the sum by Knuth's TwoSum.
+__device__ __forceinline__ void dot2_step(float a, float b, float& p, float& s) {
+  const float h = __fmul_rn(a, b);
+  const float r = __fmaf_rn(a, b, -h);
+  float q;
+  two_sum_f(p, h, p, q);
+  s = __fadd_rn(s, __fadd_rn(q, r));
+}
+
+// This thread's part of a DOT tile (A . x over n elements): elements (or
+// 16-byte packs) t, t + 256, ... in two Dot2 chains, returned in FP64.
+__device__ double dot2_part(const BatchTile& tl) {
+  const float* a = static_cast<const float*>(tl.A);
+  const float* b = tl.x;
+  const int n = tl.n;
+  float p0 = 0.f, s0 = 0.f, p1 = 0.f, s1 = 0.f;
+  int e0 = 0;
+  if (tl.vec) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    const int P = n >> 2;
+    int j = threadIdx.x;
+#pragma unroll 1
+    for (; j + kThreads < P; j += 2 * kThreads) {  // two packs of each vector in flight
+      const float4 x0 = __ldcs(a4 + j), y0 = __ldcs(b4 + j);
+      const float4 x1 = __ldcs(a4 + j + kThreads), y1 = __ldcs(b4 + j + kThreads);
+      dot2_step(x0.x, y0.x, p0, s0);
+      dot2_step(x0.y, y0.y, p1, s1);
+      dot2_step(x0.z, y0.z, p0, s0);
+      dot2_step(x0.w, y0.w, p1, s1);
+      dot2_step(x1.x, y1.x, p0, s0);
+      dot2_step(x1.y, y1.y, p1, s1);
+      dot2_step(x1.z, y1.z, p0, s0);
+      dot2_step(x1.w, y1.w, p1, s1);
+    }
+    if (j < P) {
+      const float4 x0 = __ldcs(a4 + j), y0 = __ldcs(b4 + j);
+      dot2_step(x0.x, y0.x, p0, s0);
+      dot2_step(x0.y, y0.y, p1, s1);
+      dot2_step(x0.z, y0.z, p0, s0);
+      dot2_step(x0.w, y0.w, p1, s1);
+    }
+    e0 = 4 * P;
+  }
+  for (int e = e0 + threadIdx.x; e < n; e += kThreads) dot2_step(__ldcs(a + e), __ldcs(b + e), p0, s0);
+  return __dadd_rn(__dadd_rn((double)p0, (double)s0), __dadd_rn((double)p1, (double)s1));
+}
+
 // First t in [0, T] with prefix[t] >= v (prefix[0] = 0, prefix[T] = B).
 __device__ __forceinline__ int64_t first_at_least(const int64_t* prefix, int64_t T, int64_t v) {
   int64_t lo = 0, hi = T;
@@ -397,6 +447,7 @@ __device__ __forceinline__ void stage_tiles(BatchTile* dst, const BatchTile* src
 
 __global__ void __launch_bounds__(kThreads, 3) gemv_batch_kernel(const unsigned char* __restrict__ plan) {
   __shared__ __align__(16) BatchTile stage[2][kTileChunk];
+  __shared__ double red[kThreads / 32];
   const BatchHeader* h = reinterpret_cast<const BatchHeader*>(plan);
   const int64_t T = h->tiles, B = h->total_cost;
   const BatchTile* tiles = reinterpret_cast<const BatchTile*>(plan + h->off_tiles);
@@ -429,6 +480,11 @@ __global__ void __launch_bounds__(kThreads, 3) gemv_batch_kernel(const unsigned 
       // the lanes of this thread's group (aligned run of lpr lanes of the warp)
       const unsigned mask = lpr == 32 ? 0xffffffffu : ((1u << lpr) - 1u) << (wl & ~(lpr - 1));
       const int groups = kThreads >> lg;
+      if (pb.kind == kBatchDotF32) {  // the whole block, the final sum in FP64 (uniform over the block)
+        const double v = block_sum(dot2_part(pb), red);
+        if (threadIdx.x == 0) pb.c[0] = (float)__dadd_rn((double)pb.c[0], v);
+        continue;
+      }
       if (pb.kind != kBatchGerF32 && pb.vec) {  // kBatchRowsGemv rows at a time
         constexpr int RB = kBatchRowsGemv;
         for (int r = threadIdx.x >> lg; r < pb.rows; r += RB * groups) {  // uniform over the group
@@ -511,7 +567,9 @@ inline bool active(const BatchItem& it) { return it.m > 0 && it.n > 0 && it.alph
 
 inline bool shape_ok(const BatchItem& it) {
   return it.m >= 0 && it.n >= 0 && it.m <= INT32_MAX && it.n <= INT32_MAX && it.reserved == 0 &&
-         it.reserved2 == 0 && (it.kind == kBatchGemvF32 || it.kind == kBatchGemvBF16 || it.kind == kBatchGerF32);
+         it.reserved2 == 0 &&
+         (it.kind == kBatchGemvF32 || it.kind == kBatchGemvBF16 || it.kind == kBatchGerF32 ||
+          (it.kind == kBatchDotF32 && it.m <= 1 && (it.alpha == 1.f || it.alpha == 0.f)));
 }
 
 inline int64_t count_tiles(int64_t count, const BatchItem* items, const gb_batch_tuning* table) {
@@ -640,7 +698,7 @@ int batch_plan(int64_t count, const BatchItem* items, const gb_batch_tuning* tab
     pb.n = (int32_t)it.n;
     pb.alpha = it.alpha;
     pb.kind = (uint8_t)it.kind;
-    pb.vec = aligned16(it.A) && aligned16(it.x) && (it.lda * eb) % 16 == 0;
+    pb.vec = aligned16(it.A) && aligned16(it.x) && (it.kind == kBatchDotF32 || (it.lda * eb) % 16 == 0);
     if (!active(it)) continue;
     const gb_batch_tuning& tu = table[bucket_of_item(it)];
     const int64_t R = tile_rows(it, tu);

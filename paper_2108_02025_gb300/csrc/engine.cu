@@ -282,7 +282,7 @@ Footprint footprint(const gb_request& r) {
     f.extent[0] = f.extent[1] = (int64_t)n;
     f.extent[2] = 1;
     if (!pool) {
-      add((size_t)f.ld * 4);  // x, stored as the one row of a GEMV
+      add((size_t)f.ld * 4);  // x (leading dimension rounded up like a GEMV row)
       add(n * 4);
     }
     add(4);
@@ -556,8 +556,8 @@ int gb_engine::launch_step(Slot& s, const std::vector<Part>& parts) {
   for (size_t i = 0; i < segs.size(); ++i)
     first[i + 1] = first[i] + (segs[i].count + kFillChunk - 1) / kFillChunk;
 
-  // every GEMV (FP32 or BF16 A) and DOT (a one-row FP32 GEMV) in one
-  // batched launch, with the GERs of drawn requests
+  // every GEMV (FP32 or BF16 A) and DOT (FP32 Dot2 per thread, the final
+  // sum in FP64) in one batched launch, with the GERs of drawn requests
   std::vector<BatchItem> items;
   items.reserve(parts.size());
   for (const Part& pt : parts) {
@@ -570,10 +570,11 @@ int gb_engine::launch_step(Slot& s, const std::vector<Part>& parts) {
     it.lda = q->f.ld;
     if (pool) {
       const float* P = pool_f32;
-      it.kind = r.op == GB_REQ_GEMV && r.form == GB_FORM_BF16 ? kBatchGemvBF16 : kBatchGemvF32;
+      it.kind = r.op == GB_REQ_DOT ? kBatchDotF32
+                : r.form == GB_FORM_BF16 ? kBatchGemvBF16 : kBatchGemvF32;
       it.m = r.op == GB_REQ_GEMV ? pt.rows : 1;
       it.alpha = r.op == GB_REQ_GEMV ? r.alpha : 1.0f;
-      // GEMV kinds only read A; rows [row0, row0 + rows)
+      // GEMV and DOT kinds only read A; rows [row0, row0 + rows)
       const int64_t a0 = q->pool_off[0] + pt.row0 * q->f.ld;
       it.A = it.kind == kBatchGemvBF16 ? static_cast<void*>(pool_bf16 + a0) : static_cast<void*>(pool_f32 + a0);
       it.x = P + q->pool_off[1];
@@ -586,7 +587,7 @@ int gb_engine::launch_step(Slot& s, const std::vector<Part>& parts) {
       it.x = reinterpret_cast<const float*>(q->ptr(1));
       it.c = reinterpret_cast<float*>(q->ptr(2));
     } else if (r.op == GB_REQ_DOT) {
-      it.kind = kBatchGemvF32;
+      it.kind = kBatchDotF32;
       it.m = 1;
       it.alpha = 1.0f;
       it.A = q->ptr(0);

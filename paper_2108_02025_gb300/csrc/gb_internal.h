@@ -116,6 +116,7 @@ constexpr int kColTileWaves64 = 4;
 constexpr int kBatchGemvF32 = GB_BATCH_GEMV_F32;
 constexpr int kBatchGemvBF16 = GB_BATCH_GEMV_BF16;
 constexpr int kBatchGerF32 = GB_BATCH_GER_F32;
+constexpr int kBatchDotF32 = GB_BATCH_DOT_F32;
 using BatchItem = gb_batch_item;
 size_t batch_plan_bytes(int64_t count, const BatchItem* items, const gb_batch_tuning* table);
 int batch_plan(int64_t count, const BatchItem* items, const gb_batch_tuning* table, void* plan,

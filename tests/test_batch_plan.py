@@ -313,7 +313,7 @@ def test_mixed_items_argument_checks():
     assert gb.gb_batch_plan(2, arr, None, buf, nb) == gb.GB_OK
     assert gb.gb_batch_plan(-1, arr, None, buf, nb) == -1
     assert gb.gb_batch_plan(2, None, None, buf, nb) == -2
-    for field, value in (("kind", 3), ("reserved", 1), ("reserved2", 1), ("m", -1), ("n", -2), ("lda", 9),
+    for field, value in (("kind", 4), ("reserved", 1), ("reserved2", 1), ("m", -1), ("n", -2), ("lda", 9),
                          ("A", 0), ("x", 0), ("c", 0)):
         bad = items_of(ok)
         setattr(bad[1], field, value)
@@ -343,3 +343,29 @@ def test_mixed_items_argument_checks():
     assert gb.gb_batch_plan(2, arr, None, buf[1:], nb) == -4
     assert gb.gb_batch_plan(2, arr, None, buf, nb - 16) == -5
     assert gb.gb_batch_plan_bytes(2, items_of([(7, 1, 1, 1, 1.0)] * 2), None) == 0
+
+
+def test_dot_items_plan_and_checks():
+    """GB_BATCH_DOT_F32: one tile per DOT (m = 1, alpha = 1; alpha 0 skips
+    it), its accumulator written, both vectors read; the 16-byte path needs
+    only aligned vectors (lda does not matter for one row)."""
+    specs = [(gb.BATCH_DOT_F32, 1, 16384, 16384, 1.0), (gb.BATCH_DOT_F32, 1, 37, 37, 1.0),
+             (gb.BATCH_DOT_F32, 1, 5, 5, 0.0), (gb.BATCH_GEMV_F32, 100, 40, 40, 1.0)]
+    arr = items_of(specs)
+    nb = gb.gb_batch_plan_bytes(len(specs), arr, None)
+    assert nb > 0
+    buf = aligned_buffer(nb)
+    assert gb.gb_batch_plan(len(specs), arr, None, buf, nb) == gb.GB_OK
+    h, probs, raw, prefix = decode_raw(buf)
+    assert list(probs["vec"][:2]) == [1, 1]
+    dots = raw[raw["kind"] == gb.BATCH_DOT_F32]
+    assert dots.size == 2 and np.all(dots["rows"] == 1)
+    assert sorted(dots["n"]) == [37, 16384]
+    for field, value in (("m", 2), ("alpha", 0.5), ("alpha", -1.0)):
+        bad = items_of(specs)
+        setattr(bad[0], field, value)
+        assert gb.gb_batch_plan(len(specs), bad, None, buf, nb) == -2, (field, value)
+        assert gb.gb_batch_plan_bytes(len(specs), bad, None) == 0, (field, value)
+    bad = items_of(specs)
+    bad[0].c = bad[0].A + 8      # the accumulator inside the first vector
+    assert gb.gb_batch_plan(len(specs), bad, None, buf, nb) == -2

@@ -231,3 +231,42 @@ def test_mixed_kinds_every_variant(lpr, u):
     torch.cuda.synchronize()
     for it in items:
         it.check()
+
+
+DOT_BOUND = 2.0 ** -22   # two FP32 roundings of the condition-aware scale
+
+
+@pytest.mark.parametrize("mis", [0, 1], ids=["aligned", "misaligned"])
+def test_dot_items_fp64_final_sum(mis):
+    """GB_BATCH_DOT_F32 tiles (Def. DOT; Algs. 3-4): per-thread Dot2 in FP32,
+    the threads' parts and the initial accumulator summed in FP64, one
+    rounding to FP32.  Each result within 2^-22 of |alpha0| + sum |x_p y_p|
+    of the FP64 oracle, the bound gb_sdot meets on the same inputs; mixed
+    with GEMV items in one launch."""
+    ns = [1, 3, 4, 37, 1000, 1027, 4096, 16384, 100003]
+    items, dots = [], []
+    for k, n in enumerate(ns):
+        x = synth.uniform(n, 500 + k, 1, np.float32)
+        y = synth.uniform(n, 500 + k, 2, np.float32)
+        a0 = synth.uniform(1, 500 + k, 3, np.float32)
+        out = Guarded(a0, mis)
+        dx, dy = to_dev(x, mis), to_dev(y, mis)
+        items.append((gb.BATCH_DOT_F32, dx, dy, out.view, 1.0, 1, n, n))
+        dots.append((n, x, y, a0, out, dx, dy))
+    gemv = Item(gb.BATCH_GEMV_F32, 300, 257, 0, 0.5, 77)
+    b = gb.Batch.from_items(items + [gemv.entry()])
+    b.launch()
+    torch.cuda.synchronize()
+    gemv.check()
+    for (n, x, y, a0, out, dx, dy) in dots:
+        got = float(out.result()[0])
+        want = oracle.dot(n, x, y, float(a0[0]))
+        scale = oracle.dot_scale(n, x, y, float(a0[0]))
+        assert abs(got - want) <= DOT_BOUND * scale, (n, abs(got - want) / scale)
+        # gb_sdot on the same operands meets the same bound
+        ref = Guarded(a0.copy())
+        nb = gb.gb_workspace_bytes(gb.OP_DOT, gb.F32, 0, 0, n)
+        ws = torch.zeros(max(nb, 1), dtype=torch.uint8, device="cuda")
+        assert gb.gb_sdot(n, dx, dy, ref.view, ws, nb) == gb.GB_OK
+        torch.cuda.synchronize()
+        assert abs(float(ref.result()[0]) - want) <= DOT_BOUND * scale, n

@@ -308,3 +308,38 @@ def test_pool_chunks_of_one_row():
     assert stats["steps"] >= 41
     for r, o in zip(reqs, outs):
         check_pool(r, o)
+
+
+# ------------------------------------------------------------ served DOTs --
+
+DOT_BOUND = 2.0 ** -22   # two FP32 roundings of |alpha0| + sum |x_p y_p|, as gb_sdot
+
+
+def dot_stream(count, seed, rate):
+    reqs, t = stream(count, seed, lo=32, hi=16384, rate=rate)
+    return [(gb.REQ_DOT, gb.FORM_F32, 1, n, 1.0, s) for (_, _, _, n, _, s) in reqs], t
+
+
+def test_served_dots_fp64_final_sum():
+    """DOT requests (Def. DOT; Algs. 3-4) take per-thread Dot2 in FP32 and
+    the final sum, with the initial alpha, in FP64 (the batched kernel's
+    DOT tiles): every served result within 2^-22 of the condition-aware
+    scale of the FP64 oracle, drawn and pool operands, and bit-identical
+    alone and in the mix."""
+    reqs, t = dot_stream(60, 5, rate=200000.0)
+    outs, done, _ = serve(reqs, t)
+    assert max(np.bincount([c["step"] for c in done])) > 1, "the DOTs share steps"
+    for r, o in zip(reqs, outs):
+        x, y, a0 = operands(gb.REQ_DOT, gb.FORM_F32, 1, r[3], r[5])
+        want = oracle.dot(r[3], x, y, float(a0[0]))
+        scale = oracle.dot_scale(r[3], x, y, float(a0[0]))
+        assert abs(float(o[0]) - want) <= DOT_BOUND * scale, (r, abs(float(o[0]) - want) / scale)
+    for i in (0, 9, 33):
+        alone, _, _ = serve([reqs[i]], [0], streams=1)
+        assert np.array_equal(alone[0].view(np.uint32), outs[i].view(np.uint32)), reqs[i]
+    pouts, _, _ = serve_pool(reqs, t)
+    for r, o in zip(reqs, pouts):
+        x, y, a0 = pool_operands(gb.REQ_DOT, gb.FORM_F32, 1, r[3], r[5])
+        want = oracle.dot(r[3], x, y, float(a0[0]))
+        scale = oracle.dot_scale(r[3], x, y, float(a0[0]))
+        assert abs(float(o[0]) - want) <= DOT_BOUND * scale, (r, abs(float(o[0]) - want) / scale)
