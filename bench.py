@@ -56,6 +56,7 @@ HBM_FALLBACK_GBS = 6800.0
 CPU_FRACTION = 16    # cpu_baseline sample: 1/16 of a step
 NOMINAL_HBM_GBS = 8000.0   # HBM3e data-sheet bandwidth, for a second fraction beside the measured peak
 REF_FRACTION = 32    # reference arm: 1/32 of a step per step
+OP_CALLS, OP_REPS = 10, 3   # per-operation timing: calls back to back per event pair, pairs
 SMS, DP_FMA_PER_CLK_SM, SM_MAX_MHZ = 152, 2, 2070.0   # FP64 pipe: 2 FMA/clk/SM (1.26 TFLOP/s at 2.07 GHz)
 
 
@@ -442,12 +443,19 @@ def precision_bytes(form, m, n):
     return a + 4 * n + 8 * m + (4 * m if form == "e4m3" else 0)
 
 
+def quantize_bytes(form, m, n):
+    """Compulsory bytes of one quantiser call: the FP32 master read, the codes
+    (and row scales) written."""
+    return 4 * m * n + (2 * m * n if form == "bf16" else m * n + 4 * m)
+
+
 def run_precision(device, stream, reps=20, sample_rows=64):
     """Solves/s of the 32768^2 GEMV with A stored as FP32 (plain method), BF16
     and E4M3, timed with CUDA events (median of `reps` calls; A is larger
     than L2), and the error of each form against an FP64 evaluation (numpy)
     of the FP32 master on `sample_rows` seeded rows, relative to
-    sum_j |A_ij x_j|."""
+    sum_j |A_ij x_j|.  Beside each reduced form: the time of the quantiser
+    that prepares A in it (quantize_us) and its compulsory GB/s."""
     import numpy as np
     import torch
     import synth
@@ -491,6 +499,27 @@ def run_precision(device, stream, reps=20, sample_rows=64):
                        "GB_s": round(precision_bytes(form, m, n) / t / 1e9, 1),
                        "max_rel_err": float(f"{err:.3e}"), "bound": PREC_BOUND[form]}
         if form != "fp32":
+            # the preparation of A in this form: one quantiser call into the
+            # same code buffers, timed alone (A larger than L2)
+            if form == "bf16":
+                qcall = lambda Q=Q: gb.lib().gb_quantize_bf16(m, n, A.data_ptr(), n, Q.data_ptr(), Q.stride(0),
+                                                              stream.cuda_stream)
+            else:
+                qcall = lambda Q=Q, sc=sc: gb.lib().gb_quantize_e4m3(m, n, A.data_ptr(), n, Q.data_ptr(),
+                                                                     Q.stride(0), sc.data_ptr(), stream.cuda_stream)
+            assert qcall() == 0
+            qt = []
+            for _ in range(max(5, reps // 2)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                qcall()
+                e1.record(stream)
+                e1.synchronize()
+                qt.append(e0.elapsed_time(e1) / 1e3)
+            tq = statistics.median(qt)
+            qbytes = quantize_bytes(form, m, n)
+            forms[form].update({"quantize_us": round(tq * 1e6, 2), "quantize_GB_s": round(qbytes / tq / 1e9, 1),
+                                "quantize_bytes": qbytes})
             del Q, sc
     for form in ("bf16", "e4m3"):
         forms[form]["speedup_vs_fp32"] = round(forms[form]["solves_per_s"] / forms["fp32"]["solves_per_s"], 3)
@@ -815,12 +844,17 @@ def run_ours(args):
     sh = stream.cuda_stream
     ops = wl.ops
 
+    # the operations moving the most bytes (the FP64 DOT and GERs) carry an
+    # event pair inside the timed steps: the roofline kernel is timed live
+    top = max(alg_bytes(k, dt, m, n) for (_, k, dt, _, m, n) in ops)
+    live = [i for i, (_, k, dt, _, m, n) in enumerate(ops) if alg_bytes(k, dt, m, n) == top]
+
     def step(evs=None):
         for i, op in enumerate(ops):
-            if evs is not None:
+            if evs is not None and i in evs:
                 evs[i][0].record(stream)
             wl.launch(op, sh)
-            if evs is not None:
+            if evs is not None and i in evs:
                 evs[i][1].record(stream)
 
     for _ in range(args.warmup):
@@ -831,8 +865,8 @@ def run_ours(args):
     clocks.start()
     for _ in range(2):  # keep the GPU busy while the sampler comes up
         step()
-    per_op = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
-               for _ in ops] for _ in range(args.steps)]
+    live_ev = [{i: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for i in live}
+               for _ in range(args.steps)]
     t_begin = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(device)
@@ -840,27 +874,45 @@ def run_ours(args):
     wall0 = time.time()
     t_begin.record(stream)
     for k in range(args.steps):
-        step(per_op[k])
+        step(live_ev[k])
     t_end.record(stream)
     torch.cuda.synchronize(device)
     barrier()
     wall1 = time.time()
-    clocks.stop()
     elapsed = t_begin.elapsed_time(t_end) / 1e3
     elapsed_max = max_over_ranks(elapsed, device)
 
+    # Per operation, after the timed steps: OP_CALLS calls back to back
+    # between two events, OP_REPS times.  (An event pair around every call
+    # would start each kernel from an idle stream and charge it a launch.)
+    per_op = []
+    for op in ops:
+        wl.launch(op, sh)
+        each = []
+        for _ in range(OP_REPS):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(OP_CALLS):
+                wl.launch(op, sh)
+            e1.record(stream)
+            e1.synchronize()
+            each.append(e0.elapsed_time(e1) / 1e3 / OP_CALLS)
+        per_op.append(sorted(each))
+    clocks.stop()
+
     bytes_step = sum(alg_bytes(k, dt, m, n) for (_, k, dt, _, m, n) in ops)
     value = whole_job_value(bytes_step, args.steps, world, elapsed_max)
-    op_times = [sum(per_op[k][i][0].elapsed_time(per_op[k][i][1]) for k in range(args.steps))
-                / args.steps / 1e3 for i in range(len(ops))]
+    op_times = [statistics.mean(e) for e in per_op]
+    live_times = {i: statistics.mean(live_ev[k][i][0].elapsed_time(live_ev[k][i][1]) / 1e3
+                                     for k in range(args.steps)) for i in live}
     hbm, src = peaks()
-    dom = max(range(len(ops)), key=lambda i: op_times[i])
+    dom = max(live, key=lambda i: live_times[i])   # the largest time share of the step
     ops_report = []
     for i, (name, kind, dt, lay, m, n) in enumerate(ops):
         gbs = alg_bytes(kind, dt, m, n) / op_times[i] / 1e9
-        each = sorted(per_op[k][i][0].elapsed_time(per_op[k][i][1]) * 1e3 for k in range(args.steps))
+        each = per_op[i]
         ops_report.append({"op": name, "us": round(op_times[i] * 1e6, 2),
-                           "us_median": round(each[len(each) // 2], 2), "us_min": round(each[0], 2),
+                           "us_median": round(each[len(each) // 2] * 1e6, 2), "us_min": round(each[0] * 1e6, 2),
                            "GB_s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4),
                            "frac_nominal": round(gbs / NOMINAL_HBM_GBS, 4)})
 
@@ -915,10 +967,13 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (each large operand >= 268 MB, L2 129 MB)",
                        "bytes_per_step": bytes_step},
-            "roofline": roofline_of(ops[dom], op_times[dom], hbm, src),
+            "roofline": dict(roofline_of(ops[dom], live_times[dom], hbm, src),
+                             timing="CUDA events around each launch inside the timed steps"),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": len(ops) * args.steps,
+            "ops_timing": f"after the timed steps, each operation {OP_CALLS} times back to back between two "
+                          f"CUDA events, {OP_REPS} such pairs; us = mean per call",
             "clocks": clocks.summary(wall0, wall1),
             "ops": ops_report,
             "precision": precision,
@@ -1113,8 +1168,9 @@ def case_bytes(op, dtype, m, n):
 def run_case(args):
     """One operation of the library timed on its own (--case OP DTYPE LAYOUT
     M N): inputs uniform[-1,1] from the generator (gemvq: the precision
-    workload's A, quantised before timing; batch: M GEMVs of the batched
-    workload in one launch with the tuned table).  Each rep is --batch calls
+    workload's A, quantised before timing; quant: the quantiser of DTYPE on
+    that A; batch: M GEMVs of the batched workload in one launch with the
+    tuned table).  Each rep is --batch calls
     back to back between two CUDA events on the launching stream (the
     events' resolution is about 2 us), after an L2 flush by a read of 512
     MB; the calls take copies of the operands in turn (at least 600 MB
@@ -1146,7 +1202,8 @@ def run_case(args):
             synth.fill_uniform(t, 0, s)
             return t
 
-        nb = case_bytes(op, dtype, m, n) if op != "batch" else None
+        nb = case_bytes(op, dtype, m, n) if op not in ("batch", "quant") else quantize_bytes(dtype, m, n) \
+            if op == "quant" else None
         # copies of the operands, used in turn, so that no call finds its
         # operands in L2 (together at least 4.5x the L2)
         copies = 1 if op == "batch" else max(1, min(8, -(-(600 << 20) // nb)))
@@ -1163,6 +1220,17 @@ def run_case(args):
                 C, x, y = filled(m * n, 7 + 10 * r), filled(m, 8 + 10 * r), filled(n, 9 + 10 * r)
                 ld = n if lay == gb.ROW_MAJOR else m
                 calls.append(lambda C=C, x=x, y=y, ld=ld: gb.ger(x, y, C, 1.0, lay, m, n, ld))
+            elif op == "quant":  # the quantiser of DTYPE (bf16 or e4m3) on the precision workload's A
+                A = torch.empty((m, n), dtype=torch.float32, device=device)
+                synth.fill_normal_rows(A, 0, 1 + 10 * r, -3.0, 3.0)
+                Q, sc = gb.quantize(A, dtype)
+                nb = quantize_bytes(dtype, m, n)
+                if dtype == "bf16":
+                    calls.append(lambda A=A, Q=Q: gb.lib().gb_quantize_bf16(m, n, A.data_ptr(), n, Q.data_ptr(),
+                                                                            Q.stride(0), stream.cuda_stream))
+                else:
+                    calls.append(lambda A=A, Q=Q, sc=sc: gb.lib().gb_quantize_e4m3(
+                        m, n, A.data_ptr(), n, Q.data_ptr(), Q.stride(0), sc.data_ptr(), stream.cuda_stream))
             elif op == "batch":  # M FP32 GEMVs of the batched workload in one launch; N unused
                 bw_ = BatchWorkload(device, count=m)
                 b = gb.Batch(bw_.problems, table=gb.load_tuning())
@@ -1242,7 +1310,7 @@ def main(argv=None):
     p.add_argument("--no-growth", action="store_true",
                    help="skip the reduced-precision, batched and serving legs")
     p.add_argument("--case", nargs=5, metavar=("OP", "DTYPE", "LAYOUT", "M", "N"),
-                   help="time one operation alone: OP gemv|dot|ger|gemvq|batch, DTYPE f32|f64|bf16|e4m3, "
+                   help="time one operation alone: OP gemv|dot|ger|gemvq|batch|quant, DTYPE f32|f64|bf16|e4m3, "
                         "LAYOUT row|col|-; for batch, M is the number of GEMVs")
     p.add_argument("--scale", default=None,
                    help="with --case: factors of the long dimension, e.g. 1,2,4,8, and a fit t = t0 + bytes/bw")
@@ -1264,8 +1332,8 @@ def main(argv=None):
         run_serve_case(args)
         return
     if args.case:
-        if args.case[0] not in ("gemv", "dot", "ger", "gemvq", "batch"):
-            p.error("--case OP must be gemv, dot, ger, gemvq or batch")
+        if args.case[0] not in ("gemv", "dot", "ger", "gemvq", "batch", "quant"):
+            p.error("--case OP must be gemv, dot, ger, gemvq, batch or quant")
         run_case(args)
         return
     if args.warmup < 3 and args.impl == "ours":

@@ -252,8 +252,9 @@ inline ColShape col_shape(size_t e, bool vec, int64_t m, int64_t n) {
   ColShape c;
   if (vec) {  // block tiles of tx*V rows; tx threads along the rows, 256/tx along the columns
     // short columns (n small): up to all 256 threads along the rows, no
-    // cross-lane sum; otherwise at most 64
-    const int64_t tx = pow2_at_least(cdiv(m, V), n <= kColShortN ? 256 : 64);
+    // cross-lane sum (FP64: up to 128, so that a tile is smaller and the
+    // last wave of tiles shorter); otherwise at most 64
+    const int64_t tx = pow2_at_least(cdiv(m, V), n <= kColShortN ? (e == 8 ? 128 : 256) : 64);
     const int64_t ty = 256 / tx;
     c.txw = (int)tx;
     c.sp = block_split(cdiv(m, tx * V), n, ty * kColTileU, 1, e, kWaveBlocks, kColMinUnits);

@@ -154,7 +154,14 @@ __global__ void __launch_bounds__(kThreads, 4)
     double s = 0.0;  // block totals, in index order per thread, then block_sum's fixed order
     const int per = (gridDim.x + kThreads - 1) / kThreads;
     const int b0 = threadIdx.x * per;
-    for (int b = b0; b < b0 + per && b < (int)gridDim.x; ++b) s = __dadd_rn(s, __ldcg(part + b));
+    for (int b = b0; b < b0 + per; b += 4) {  // four loads in flight, added in index order
+      double v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] = b + i < b0 + per && b + i < (int)gridDim.x ? __ldcg(part + b + i) : 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (b + i < b0 + per && b + i < (int)gridDim.x) s = __dadd_rn(s, v[i]);
+    }
     const double total = block_sum(s, red);
     if (threadIdx.x == 0) {
       *alpha = (T)__dadd_rn((double)*alpha, total);

@@ -281,7 +281,14 @@ __device__ __forceinline__ void warp_sum_rows_p(const double* src, int64_t strid
     const int r = rb + lane / P;
     double s = 0.0;
     if (r < rows)
-      for (int q = k; q < count; q += P) s = __dadd_rn(s, __ldcg(src + (int64_t)q * stride + row0 + r));
+      for (int q = k; q < count; q += 4 * P) {  // four loads in flight, added in index order
+        double v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = q + i * P < count ? __ldcg(src + (int64_t)(q + i * P) * stride + row0 + r) : 0.0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (q + i * P < count) s = __dadd_rn(s, v[i]);
+      }
     s = group_sum<P>(s);
     if (k == 0 && r < rows) sink(row0 + r, s);
   }
@@ -321,15 +328,16 @@ __device__ void block_sum_rows(const double* src, int64_t stride, int count, int
       const int q0 = slice * per;
       const int q1 = q0 + per < count ? q0 + per : count;
       const double* p = src + row0 + r;
-      int q = q0;
-      for (; q + 8 <= q1; q += 8) {  // eight loads in flight, added in order
+      // up to eight loads in flight (the last batch predicated), then added
+      // in index order: one L2 round trip per eight partials
+      for (int q = q0; q < q1; q += 8) {
         double v[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = __ldcg(p + (int64_t)(q + k) * stride);
+        for (int k = 0; k < 8; ++k) v[k] = q + k < q1 ? __ldcg(p + (int64_t)(q + k) * stride) : 0.0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc = __dadd_rn(acc, v[k]);
+        for (int k = 0; k < 8; ++k)
+          if (q + k < q1) acc = __dadd_rn(acc, v[k]);
       }
-      for (; q < q1; ++q) acc = __dadd_rn(acc, __ldcg(p + (int64_t)q * stride));
     }
     __syncthreads();
     red[threadIdx.x] = acc;

@@ -46,27 +46,70 @@ struct Fmt {
 
 // ------------------------------------------------------------ quantisers ---
 
+// BF16 codes of a row-major FP32 matrix.  A unit is a chunk of kQChunk
+// columns of one row; block b takes the units b, b + G, ...  With A and Q
+// rows on 16 bytes each thread converts two packs of 8 elements (two 16-byte
+// loads, one 16-byte store each); other rows, and the columns past the last
+// whole pack, go element by element.  Rounding: __float2bfloat16_rn.
+constexpr int64_t kQChunk = (int64_t)kThreads * 16;
+
+__device__ __forceinline__ unsigned bf16_pair(float lo, float hi) {
+  const __nv_bfloat16 a = __float2bfloat16_rn(lo), b = __float2bfloat16_rn(hi);
+  return (unsigned)*reinterpret_cast<const uint16_t*>(&a) | ((unsigned)*reinterpret_cast<const uint16_t*>(&b) << 16);
+}
+
 __global__ void __launch_bounds__(kThreads)
     quantize_bf16_kernel(int64_t m, int64_t n, const float* __restrict__ A, int64_t lda,
-                         uint16_t* __restrict__ Q, int64_t ldq) {
-  const int64_t total = m * n;
-  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * kThreads) {
-    const int64_t i = e / n, j = e - i * n;
-    const __nv_bfloat16 b = __float2bfloat16_rn(__ldcs(A + i * lda + j));
-    Q[i * ldq + j] = *reinterpret_cast<const uint16_t*>(&b);
+                         uint16_t* __restrict__ Q, int64_t ldq, int64_t chunks, bool vec) {
+  const int64_t units = m * chunks;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t i = u / chunks;
+    const int64_t k0 = (u - i * chunks) * kQChunk;
+    const int64_t k1 = k0 + kQChunk < n ? k0 + kQChunk : n;
+    const float* Ar = A + i * lda;
+    uint16_t* Qr = Q + i * ldq;
+    int64_t kv = k0;  // columns from here on go element by element
+    if (vec) {
+      const int64_t whole = k0 + (k1 - k0) / 8 * 8;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t j = k0 + ((int64_t)h * kThreads + threadIdx.x) * 8;
+        if (j < whole) {
+          const float4 a0 = __ldcs(reinterpret_cast<const float4*>(Ar + j));
+          const float4 a1 = __ldcs(reinterpret_cast<const float4*>(Ar + j + 4));
+          const uint4 q = make_uint4(bf16_pair(a0.x, a0.y), bf16_pair(a0.z, a0.w), bf16_pair(a1.x, a1.y),
+                                     bf16_pair(a1.z, a1.w));
+          __stcs(reinterpret_cast<uint4*>(Qr + j), q);
+        }
+      }
+      kv = whole;
+    }
+    for (int64_t j = kv + threadIdx.x; j < k1; j += kThreads) {
+      const __nv_bfloat16 b = __float2bfloat16_rn(__ldcs(Ar + j));
+      Qr[j] = *reinterpret_cast<const uint16_t*>(&b);
+    }
   }
 }
 
-// One block per row: the row's absolute maximum, then the codes.
+// E4M3 codes and row scales: rows b, b + G, ... per block; the row's
+// absolute maximum (the row is read through L2, so that its second reading
+// for the codes finds it there), the scale s = fl32(amax / 448), then the
+// codes E4M3_satfinite(fl32(A_ij / s)), four per 16-byte load when A and Q
+// rows allow it.
 __global__ void __launch_bounds__(kThreads)
     quantize_e4m3_kernel(int64_t m, int64_t n, const float* __restrict__ A, int64_t lda,
-                         uint8_t* __restrict__ Q, int64_t ldq, float* __restrict__ scales) {
+                         uint8_t* __restrict__ Q, int64_t ldq, float* __restrict__ scales, bool vec) {
   __shared__ float red[kThreads / 32];
+  const int64_t nv = vec ? n / 4 * 4 : 0;  // columns read four at a time
   for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
     const float* Ar = A + i * lda;
+    uint8_t* Qr = Q + i * ldq;
     float amax = 0.f;
-    for (int64_t j = threadIdx.x; j < n; j += kThreads) amax = fmaxf(amax, fabsf(Ar[j]));
+    for (int64_t j = (int64_t)threadIdx.x * 4; j < nv; j += (int64_t)kThreads * 4) {
+      const float4 a = __ldcg(reinterpret_cast<const float4*>(Ar + j));
+      amax = fmaxf(amax, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))));
+    }
+    for (int64_t j = nv + threadIdx.x; j < n; j += kThreads) amax = fmaxf(amax, fabsf(__ldcg(Ar + j)));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     __syncthreads();
@@ -77,11 +120,14 @@ __global__ void __launch_bounds__(kThreads)
     for (int w = 0; w < kThreads / 32; ++w) amax = fmaxf(amax, red[w]);
     const float s = __fdiv_rn(amax, 448.0f);
     if (threadIdx.x == 0) scales[i] = s;
-    for (int64_t j = threadIdx.x; j < n; j += kThreads) {
-      uint8_t q = 0;
-      if (s != 0.f) q = (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(Ar[j], s), __NV_SATFINITE, __NV_E4M3);
-      Q[i * ldq + j] = q;
+    auto code = [&](float v) -> unsigned {
+      return s != 0.f ? (unsigned)__nv_cvt_float_to_fp8(__fdiv_rn(v, s), __NV_SATFINITE, __NV_E4M3) : 0u;
+    };
+    for (int64_t j = (int64_t)threadIdx.x * 4; j < nv; j += (int64_t)kThreads * 4) {
+      const float4 a = __ldcs(reinterpret_cast<const float4*>(Ar + j));
+      *reinterpret_cast<unsigned*>(Qr + j) = code(a.x) | (code(a.y) << 8) | (code(a.z) << 16) | (code(a.w) << 24);
     }
+    for (int64_t j = nv + threadIdx.x; j < n; j += kThreads) Qr[j] = (uint8_t)code(__ldcs(Ar + j));
   }
 }
 
@@ -277,15 +323,20 @@ __global__ void __launch_bounds__(kThreads, MINB)
 
 int quantize_bf16_launch(int64_t m, int64_t n, const float* A, int64_t lda, uint16_t* Q,
                          int64_t ldq, cudaStream_t st) {
-  const int grid = grid_size((const void*)quantize_bf16_kernel, (m * n + kThreads - 1) / kThreads);
-  quantize_bf16_kernel<<<grid, kThreads, 0, st>>>(m, n, A, lda, Q, ldq);
+  const bool vec = (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && (reinterpret_cast<uintptr_t>(Q) & 15u) == 0 &&
+                   lda % 4 == 0 && ldq % 8 == 0;
+  const int64_t chunks = (n + kQChunk - 1) / kQChunk;
+  const int grid = grid_size((const void*)quantize_bf16_kernel, m * chunks);
+  quantize_bf16_kernel<<<grid, kThreads, 0, st>>>(m, n, A, lda, Q, ldq, chunks, vec);
   return 0;
 }
 
 int quantize_e4m3_launch(int64_t m, int64_t n, const float* A, int64_t lda, uint8_t* Q,
                          int64_t ldq, float* scales, cudaStream_t st) {
+  const bool vec = (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && (reinterpret_cast<uintptr_t>(Q) & 3u) == 0 &&
+                   lda % 4 == 0 && ldq % 4 == 0;
   const int grid = grid_size((const void*)quantize_e4m3_kernel, m);
-  quantize_e4m3_kernel<<<grid, kThreads, 0, st>>>(m, n, A, lda, Q, ldq, scales);
+  quantize_e4m3_kernel<<<grid, kThreads, 0, st>>>(m, n, A, lda, Q, ldq, scales, vec);
   return 0;
 }
 
