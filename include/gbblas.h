@@ -60,9 +60,10 @@
  * uses a compensated FP32 dot product per thread and FP64 above that; FP64
  * GEMV and DOT form part of their products in FP64 and part exactly with
  * FP32 instructions (each operand cut into two FP32 parts, TwoProduct,
- * TwoSum into an FP32 pair folded into the FP64 sum every 32 products or
- * fewer; each such product within 2^-45 of exact), operands outside
- * 2^-30 <= |v| < 2^31 always in FP64; the last reduction of DOT is FP64.
+ * TwoSum into an FP32 pair folded into the FP64 sum every 16 products or
+ * fewer; each such product within 2.5 * 2^-45 of exact, each pair within
+ * 7.8e-13 of the sum of |a x| of its products), operands outside
+ * 2^-30 <= |v| < 2^34 always in FP64; the last reduction of DOT is FP64.
  *
  * Fault injection (host side, for failure tests): GB_FAULT_INJECT=<op>:<k>
  * with <op> one of gemv, dot, ger makes the k-th call (1-based, counted per

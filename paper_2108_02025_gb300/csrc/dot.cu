@@ -98,12 +98,12 @@ __global__ void __launch_bounds__(kThreads, 4)
       for (int q = 0; q < QE; ++q)
 #pragma unroll
         for (int v = 0; v < V; ++v) acc.add(xp[q].v[v], yp[q].v[v], q * V + v);
-      bool ok = true;
+      unsigned rb = 0u;  // the emulated operands' ranges, OR-ed
 #pragma unroll
       for (int q = QE; q < U; ++q)
 #pragma unroll
-        for (int v = 0; v < V; ++v) ok = ok && emu_ok(xp[q].v[v]) && emu_ok(yp[q].v[v]);
-      if (__all_sync(__activemask(), ok)) {
+        for (int v = 0; v < V; ++v) rb |= emu_range(xp[q].v[v]) | emu_range(yp[q].v[v]);
+      if (__all_sync(__activemask(), rb < kEmuRange)) {
 #pragma unroll
         for (int q = QE; q < U; ++q)
 #pragma unroll

@@ -109,25 +109,35 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 // 24-bit head and the next 23 bits (emu_split, integer operations on the
 // bit pattern, exact), the head product is formed exactly with an FMA
 // (TwoProduct), the two cross terms are added in FP32, and the running sum
-// is an unevaluated FP32 pair (H, L) updated with Knuth's TwoSum.  Dropped
-// parts are below 2^-45 of |a*x| per product; the pair is folded into the
-// FP64 sum every 32 products or fewer.  Operands outside 2^-30 <= |v| < 2^31 (zero,
+// is an unevaluated FP32 pair (H, L) updated with Knuth's TwoSum.  The
+// operand cuts drop below 3*2^-46 of |a*x| per product and the rounding of
+// the cross terms below 2^-45; the pair is folded into the FP64 sum every
+// kEmuChain products or fewer.  Operands outside 2^-30 <= |v| < 2^34 (zero,
 // subnormal, huge, Inf, NaN) take the FP64 FMA instead (emu_ok).
 
-__device__ __forceinline__ bool emu_ok(double v) {
-  const unsigned e = ((unsigned)__double2hiint(v) >> 20) & 0x7FFu;
-  return e - 993u <= 60u;  // biased exponent in [993, 1053]
+// Range of the emulated operands: the biased FP64 exponent in [993, 1056],
+// i.e. 2^-30 <= |v| < 2^34.  emu_range(v) is below kEmuRange exactly for
+// those: a valid operand sets bits below bit 26 only, any other some bit at
+// 26 or above, so OR-ing several operands' values and comparing once tests
+// them all.
+constexpr unsigned kEmuRange = 64u << 20;
+__device__ __forceinline__ unsigned emu_range(double v) {
+  return ((unsigned)__double2hiint(v) & 0x7FF00000u) - (993u << 20);
 }
+__device__ __forceinline__ bool emu_ok(double v) { return emu_range(v) < kEmuRange; }
 
 // v == hi + lo + r with |r| < 2^-46 |v|: hi = v truncated to 24 significant
-// bits, lo = the next 23 bits.  Requires emu_ok(v).
+// bits, lo = the next 23 bits.  Requires emu_ok(v).  In that range the
+// rebiased exponent fits 8 bits, so the funnel shift leaves bit 31 clear for
+// the sign; lo is (its 23 bits with hi's sign and exponent - 23) minus the
+// implicit leading one, an exact subtraction.
 __device__ __forceinline__ void emu_split(double v, float& hi, float& lo) {
   const unsigned h = (unsigned)__double2hiint(v), l = (unsigned)__double2loint(v);
-  const unsigned sgn = h & 0x80000000u;
   const unsigned f = __funnelshift_l(l, h - (896u << 20), 3);  // rebias 1023 -> 127, shift into place
-  hi = __uint_as_float((f & 0x7FFFFFFFu) | sgn);
-  const unsigned ge = (f & 0x7F800000u) - (23u << 23);         // exponent 23 below hi's
-  lo = __fsub_rn(__uint_as_float(sgn | ge | ((l >> 6) & 0x7FFFFFu)), __uint_as_float(sgn | ge));
+  const unsigned hb = f | (h & 0x80000000u);
+  hi = __uint_as_float(hb);
+  const unsigned sg = (hb & 0xFF800000u) - (23u << 23);        // sign, exponent 23 below hi's
+  lo = __fsub_rn(__uint_as_float(sg | ((l >> 6) & 0x7FFFFFu)), __uint_as_float(sg));
 }
 
 // (H, L) += a*x with FP32 instructions only; requires emu_ok(a) && emu_ok(x).

@@ -37,6 +37,11 @@ constexpr int kRowMultiB = 4;
 constexpr int kRowMultiMinRows = 16;  // fewer FP64 rows take the one-row long kernel
 constexpr int kRowShortD64 = 2;  // FP64 short rows: of a lane's 8 packs, those on the FP64 pipe
 constexpr int kRowShortB64 = 4;  // FP64 short rows: resident blocks per SM budgeted for
+// Short rows: the next row block's packs loaded while the current one is
+// summed (FP64, FP32), and the resident blocks per SM budgeted for then.
+constexpr bool kRowShortPf64 = false;
+constexpr bool kRowShortPf32 = true;
+constexpr int kRowShortPfB = 2;
 constexpr int64_t kRowShortPPL = 8;  // short rows: packs per lane the lanes per row are sized for (<= 8)
 constexpr int kRowScalarRW = 4;  // rows per lane group, misaligned row-major kernel
 constexpr int kColTileU = 8;     // columns in flight per thread, column-major tile kernel

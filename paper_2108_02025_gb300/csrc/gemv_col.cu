@@ -206,13 +206,14 @@ __global__ void __launch_bounds__(kThreads, 4)
           for (int q = 0; q < DU; ++q)
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = fma_rn(ap[q].v[v], xs[q], acc[v]);
-          bool ok = true;
+          unsigned rb = 0u;  // the emulated operands' ranges, OR-ed
 #pragma unroll
           for (int q = DU; q < U; ++q) {
-            ok = ok && emu_ok(xs[q]);
+            rb |= emu_range(xs[q]);
 #pragma unroll
-            for (int v = 0; v < V; ++v) ok = ok && emu_ok(ap[q].v[v]);
+            for (int v = 0; v < V; ++v) rb |= emu_range(ap[q].v[v]);
           }
+          const bool ok = rb < kEmuRange;
           // the choice is made for all the lanes that run here together (the
           // active mask: lanes of one warp may leave this loop at different
           // trips), so that the emulated path holds no FP64 instruction (a

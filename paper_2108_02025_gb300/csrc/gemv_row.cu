@@ -104,12 +104,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowLongB64 : 4)
             if (v == 0) acc = fma_rn(ap[q].v[v], xp[q].v[v], acc);
             else acc2 = fma_rn(ap[q].v[v], xp[q].v[v], acc2);
           }
-        bool ok = true;
+        unsigned rb = 0u;  // the emulated operands' ranges, OR-ed
 #pragma unroll
         for (int q = UD; q < U; ++q)
 #pragma unroll
-          for (int v = 0; v < V; ++v) ok = ok && emu_ok(ap[q].v[v]) && emu_ok(xp[q].v[v]);
-        if (__all_sync(__activemask(), ok)) {
+          for (int v = 0; v < V; ++v) rb |= emu_range(ap[q].v[v]) | emu_range(xp[q].v[v]);
+        if (__all_sync(__activemask(), rb < kEmuRange)) {
 #pragma unroll
           for (int q = UD; q < U; ++q)
 #pragma unroll
@@ -389,16 +389,16 @@ __global__ void __launch_bounds__(kThreads, kRowMultiB)
           acc[r] = __fma_rn(ap[r][q].v[0], xp[q].v[0], acc[r]);
           acc2[r] = __fma_rn(ap[r][q].v[1], xp[q].v[1], acc2[r]);
         }
-      bool ok = true;
+      unsigned rb = 0u;  // the emulated operands' ranges, OR-ed
 #pragma unroll
       for (int q = D; q < U; ++q)
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          ok = ok && emu_ok(xp[q].v[v]);
+          rb |= emu_range(xp[q].v[v]);
 #pragma unroll
-          for (int r = 0; r < R; ++r) ok = ok && emu_ok(ap[r][q].v[v]);
+          for (int r = 0; r < R; ++r) rb |= emu_range(ap[r][q].v[v]);
         }
-      if (__all_sync(__activemask(), ok)) {
+      if (__all_sync(__activemask(), rb < kEmuRange)) {
 #pragma unroll
         for (int q = D; q < U; ++q)
 #pragma unroll
@@ -477,8 +477,8 @@ __global__ void __launch_bounds__(kThreads, kRowMultiB)
 // Short rows (S = 1, at most 32*8 packs).  LPR lanes per row, each with up
 // to 8 packs (pack k*LPR + l of the row), so a block iteration reads
 // 256/LPR consecutive rows; block b takes the row blocks b, b + G, ....
-template <typename T, int V, int LPR>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowShortB64 : 4)
+template <typename T, int V, int LPR, bool PF>
+__global__ void __launch_bounds__(kThreads, PF ? kRowShortPfB : (sizeof(T) == 8 ? kRowShortB64 : 4))
     gemv_row_short_kernel(int64_t m, int64_t n, T alpha, const T* __restrict__ A, int64_t lda,
                           const T* __restrict__ x, T* __restrict__ c) {
   constexpr int GROUPS = kThreads / LPR;  // rows per block iteration
@@ -506,16 +506,35 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowShortB64 : 4)
 
   // every thread runs the same number of iterations (the butterfly needs
   // whole warps); rows past m are predicated off
+  // this lane's packs of the row block at row b (PF: the next row block's
+  // packs are loaded before the current one is summed, so loads stay in
+  // flight through the arithmetic)
+  const int64_t bstep = (int64_t)gridDim.x * GROUPS;
+  auto load = [&](int64_t b, Pack<T, V>(&dst)[PMAX]) {
+    const int64_t rw = b + g;
+    if (b < m && rw < m) {
+      const T* Ab = A + rw * lda;
+#pragma unroll
+      for (int k = 0; k < PMAX; ++k) {
+        const int64_t p = (int64_t)k * LPR + l;
+        if (p < packs) dst[k] = ld_stream<T, V>(Ab + p * V);
+      }
+    }
+  };
+  Pack<T, V> nxt[PMAX];
+  if constexpr (PF) load(blockIdx.x * (int64_t)GROUPS, nxt);
 #pragma unroll 1
-  for (int64_t base = blockIdx.x * (int64_t)GROUPS; base < m; base += (int64_t)gridDim.x * GROUPS) {
+  for (int64_t base = blockIdx.x * (int64_t)GROUPS; base < m; base += bstep) {
     const int64_t row = base + g;
     const bool ok = row < m;
     const T* Ar = A + (ok ? row : base) * lda;
     Pack<T, V> ap[PMAX];
+    if constexpr (PF) {
 #pragma unroll
-    for (int k = 0; k < PMAX; ++k) {
-      const int64_t p = (int64_t)k * LPR + l;
-      if (ok && p < packs) ap[k] = ld_stream<T, V>(Ar + p * V);
+      for (int k = 0; k < PMAX; ++k) ap[k] = nxt[k];
+      load(base + bstep, nxt);
+    } else {
+      load(base, ap);
     }
     T acc = (ok && tail) ? __ldcs(Ar + kv1 + l) * xt : T(0);
     if constexpr (V > 2) {  // FP32: up to 3 ragged columns, and as few as 1 or 2 lanes per row
@@ -537,16 +556,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowShortB64 : 4)
         }
       }
       // packs past the row or of a row past m take no part (they add 0)
-      bool good = true;
+      unsigned rb = 0u;  // the emulated operands' ranges, OR-ed (x: its cut is NaN when out of range)
+      bool xbad = false;
 #pragma unroll
       for (int k = PD; k < PMAX; ++k) {
         const int64_t p = (int64_t)k * LPR + l;
         if (ok && p < packs) {
 #pragma unroll
-          for (int v = 0; v < V; ++v) good = good && emu_ok(ap[k].v[v]) && !isnan(xs[p * V + v].x);
+          for (int v = 0; v < V; ++v) {
+            rb |= emu_range(ap[k].v[v]);
+            xbad = xbad || isnan(xs[p * V + v].x);
+          }
         }
       }
-      if (__all_sync(__activemask(), good)) {
+      if (__all_sync(__activemask(), rb < kEmuRange && !xbad)) {
         float eh = 0.f, el = 0.f;
 #pragma unroll
         for (int k = PD; k < PMAX; ++k) {
@@ -737,7 +760,7 @@ int launch_long(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
 
 template <typename T, int V, int LPR>
 int launch_short(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
-  auto kern = gemv_row_short_kernel<T, V, LPR>;
+  auto kern = gemv_row_short_kernel<T, V, LPR, (sizeof(T) == 8 ? kRowShortPf64 : kRowShortPf32)>;
   constexpr int64_t rows_per_iter = kThreads / LPR;
   const int grid = grid_size((const void*)kern, (a.m + rows_per_iter - 1) / rows_per_iter);
   kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c);

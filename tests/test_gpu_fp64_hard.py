@@ -14,9 +14,10 @@ most 16 products.  Three input classes aim at the weak points of that:
   TwoSum errors are largest;
 * logu: magnitudes log-uniform over [2^-60, 2^60] with random signs, so the
   floor of each emulated product's error shows beside the small terms;
-* mixed: uniform[-1,1] with zeros, subnormals and values of magnitude
-  2^31 and more mixed in, so the warp vote moves groups of products between
-  the emulated path and the FP64 fallback in the middle of a row.
+* mixed: uniform[-1,1] with zeros, subnormals, values below 2^-30 and values
+  of magnitude 2^31 to 2^39 (across the top of the emulated range, 2^34)
+  mixed in, so the warp vote moves groups of products between the emulated
+  path and the FP64 fallback in the middle of a row.
 
 Each shape selects one kernel: one-row long rows (fewer than 16 rows), the
 row-group kernel (with and without column splits), short rows, realigned
@@ -120,7 +121,8 @@ def test_dot_hard_inputs(kind, n):
 def test_hard_classes_reach_the_emulation_limits():
     """The classes are what they claim: chains are positive and within
     2^-10 below a power of two; logu spans both ends of the emulated
-    range; mixed holds zeros, subnormals and values past 2^31."""
+    range; mixed holds zeros, subnormals and values on both sides of
+    2^34, the top of the emulated range."""
     c = hard("chains", 10000, 1, 1)
     assert np.all(c > 0)
     top = np.exp2(np.ceil(np.log2(c)))
@@ -130,5 +132,6 @@ def test_hard_classes_reach_the_emulation_limits():
     mx = hard("mixed", 10000, 1, 1)
     assert np.any(mx == 0.0)
     assert np.any((mx != 0) & (np.abs(mx) < np.finfo(np.float64).tiny))
-    assert np.any(np.abs(mx) >= 2.0 ** 31)
+    assert np.any(np.abs(mx) >= 2.0 ** 34)
+    assert np.any((np.abs(mx) >= 2.0 ** 31) & (np.abs(mx) < 2.0 ** 34))
     assert np.any((np.abs(mx) > 0) & (np.abs(mx) < 2.0 ** -30) & (np.abs(mx) >= np.finfo(np.float64).tiny))
