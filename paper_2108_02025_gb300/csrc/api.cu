@@ -242,6 +242,8 @@ inline RowShape row_shape(size_t e, int al, int64_t m, int64_t n) {
 struct ColShape {
   int txw;
   bool long_chain;
+  int cluster = 0;     // CTAs per cluster (kColCluster) or 0
+  int64_t chunks = 0;  // cluster > 0: column chunks (= blocks); sp then describes the cluster partials
   SplitShape sp;
 };
 
@@ -258,6 +260,19 @@ inline ColShape col_shape(size_t e, bool vec, int64_t m, int64_t n) {
     const int64_t ty = 256 / tx;
     c.txw = (int)tx;
     c.sp = block_split(cdiv(m, tx * V), n, ty * kColTileU, 1, e, kWaveBlocks, kColMinUnits);
+    if (c.sp.items == 1 && c.sp.S > 1 && tx * V <= 256) {
+      // one row tile, columns split: chunks in clusters of kColCluster CTAs,
+      // one partial per cluster (a single level of the final sum)
+      const int64_t chunks = cdiv(c.sp.S, kColCluster) * kColCluster;
+      const int64_t kc = cdiv(n, chunks);
+      c.cluster = kColCluster;
+      c.chunks = chunks;
+      const int64_t parts = chunks / kColCluster;
+      c.sp.S = (int)parts;
+      c.sp.G = (int)parts;
+      c.sp.NG = 1;
+      c.sp.kc = kc;
+    }
     c.long_chain = e == 4 && cdiv(c.sp.kc, ty) > 64;
     return c;
   }
@@ -410,10 +425,12 @@ int gemv(int layout, int64_t m, int64_t n, T alpha, const T* A, int64_t lda, con
     p.kind = GemvPlan::kCol;
     p.txw = cs.txw;
     p.long_chain = cs.long_chain;
+    p.cluster = cs.cluster;
     s = cs.sp;
   }
   p.kc = s.kc;
   p.units = s.items * s.S;
+  if (p.cluster > 0) p.units = s.S * (int64_t)p.cluster;  // one column chunk per CTA
   p.split = split_view(s, m, ws);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (layout == GB_ROW_MAJOR) gemv_row_launch<T>(a, p, st);

@@ -32,7 +32,7 @@ constexpr int kRowLongB64 = 4;   // FP64 long-row kernel: resident blocks per SM
 // resident blocks per SM.
 constexpr int kRowMultiR = 2;
 constexpr int kRowMultiU = 4;
-constexpr int kRowMultiD = 2;
+constexpr int kRowMultiD = 1;
 constexpr int kRowMultiB = 4;
 constexpr int kRowMultiMinRows = 16;  // fewer FP64 rows take the one-row long kernel
 constexpr int kRowShortD64 = 2;  // FP64 short rows: of a lane's 8 packs, those on the FP64 pipe
@@ -46,6 +46,11 @@ constexpr int64_t kRowShortPPL = 8;  // short rows: packs per lane the lanes per
 constexpr int kRowScalarRW = 4;  // rows per lane group, misaligned row-major kernel
 constexpr int kColTileU = 8;     // columns in flight per thread, column-major tile kernel
 constexpr int kColTileD64 = 4;   // FP64: of those, columns formed on the FP64 pipe (the rest emulated)
+constexpr int kColTileD64Short = 2;  // the same for tiles of 128 or more rows (n <= kColShortN)
+// Column-major GEMVs whose rows fit one tile and whose columns are split:
+// CTAs per thread-block cluster (partials summed in distributed shared
+// memory, one partial per cluster left for the final sum).
+constexpr int kColCluster = 8;
 constexpr int64_t kColShortN = 512;  // column-major: n up to this takes tiles of up to 256 row threads
 constexpr int64_t kColMinUnits = 1;  // column-major: split until at least this many units per block
 constexpr int64_t kRowMinUnits = 2;  // row-major long rows: the same
@@ -67,6 +72,8 @@ struct GemvPlan {
   bool multi;       // FP64 long rows: the kernel with kRowMultiR rows per unit
   int lpr;          // row-major short / scalar: lanes per row (1..32)
   int txw;          // column-major: lanes along the rows of a warp item (1..32)
+  int cluster;      // column-major block tiles: CTAs per cluster summing their partials in
+                    // distributed shared memory (0: none); units are then the column chunks
   int64_t kc;       // columns per chunk
   int64_t units;    // work units (kRowLong: m * S; warp kernels: items * S)
   Split split;      // S chunks of the summed index (S = 1: no split) and their workspace

@@ -13,6 +13,10 @@
 // butterfly of shuffles; when the columns are split into S > 1 chunks the
 // chunk partials are summed in a fixed order by the warp that finishes a row
 // item last.  Warps work on items independently (grid-stride over items).
+#include <mutex>
+
+#include <cooperative_groups.h>
+
 #include "gb_common.cuh"
 #include "gb_internal.h"
 
@@ -153,7 +157,14 @@ __global__ void __launch_bounds__(kThreads, 3)
 // through shared memory in ty order; S > 1 chunk partials are combined by
 // block_split_finish.  FP32 sums stay in FP32 (chains of at most 64
 // products, then a compensated FP32 sum).
-template <typename T, int V, int TX, int U, bool LONG>
+//
+// With CL > 0 (one row tile, the columns split into `units` chunks, a launch
+// in thread-block clusters of CL CTAs) each CTA streams one chunk; the CTAs
+// of a cluster leave their partial vectors in shared memory, CTA rank 0 sums
+// them in rank order through distributed shared memory (the cluster barrier
+// is hardware: every CTA of a cluster runs at once) and writes one partial
+// per cluster, and the last cluster to finish sums those in cluster order.
+template <typename T, int V, int TX, int U, bool LONG, int CL>
 __global__ void __launch_bounds__(kThreads, 4)
     gemv_col_tile_kernel(int64_t m, int64_t n, T alpha, const T* __restrict__ A, int64_t lda,
                          const T* __restrict__ x, T* __restrict__ c, const Split sp, int64_t KC,
@@ -161,15 +172,18 @@ __global__ void __launch_bounds__(kThreads, 4)
   constexpr int TY = kThreads / TX;
   constexpr int RT = TX * V;  // rows per tile
   constexpr int FLUSH = LONG ? (64 / U > 0 ? 64 / U : 1) : 1 << 30;
-  constexpr int DU = sizeof(T) == 8 ? kColTileD64 : U;  // FP64: columns on the FP64 pipe per iteration
+  // FP64: columns on the FP64 pipe per iteration (tiles of 128 or more rows
+  // occur only with few columns, where more emulation measured faster)
+  constexpr int DU = sizeof(T) == 8 ? (TX >= 128 ? kColTileD64Short : kColTileD64) : U;
   constexpr int EFLUSH = U > DU && kEmuChain / (U - DU) > 0 ? kEmuChain / (U - DU) : 1;
   __shared__ T redT[kThreads * V];
   __shared__ double red_d[kThreads];
+  __shared__ double cpart[CL > 0 ? TX * V : 1];  // CL: this CTA's partial vector
   __shared__ int flag;
 
   const int tx = threadIdx.x % TX;
   const int ty = threadIdx.x / TX;
-  const int S = sp.S;
+  const int S = CL > 0 ? (int)units : sp.S;  // column chunks per row tile
   const int64_t cstep = (int64_t)TY * lda;  // between a thread's columns
 
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {  // interleaved units
@@ -311,21 +325,111 @@ __global__ void __launch_bounds__(kThreads, 4)
       T t = T(0);
       for (int y = 0; y < TY; ++y) t = t + redT[y * RT + r];
       const int64_t row = rt * RT + r;
-      if (row < m) {
+      if constexpr (CL > 0) {
+        cpart[r] = (double)t;
+      } else if (row < m) {
         if (S == 1) c[row] = update(c[row], alpha, t);
         else sp.part[(int64_t)s * m + row] = (double)t;
       }
     }
-    if (S > 1) {
+    if constexpr (CL > 0) {
+      namespace cg = cooperative_groups;
+      cg::cluster_group cluster = cg::this_cluster();
+      cluster.sync();  // every CTA of the cluster holds its partial vector
+      const bool lead = cluster.block_rank() == 0;
+      const int64_t q = blockIdx.x / CL;  // the cluster's partial
+      if (lead) {
+        for (int r = threadIdx.x; r < RT && r < m; r += kThreads) {
+          double v = 0.0;
+#pragma unroll
+          for (int k = 0; k < CL; ++k) v = __dadd_rn(v, *cluster.map_shared_rank(&cpart[r], k));
+          if (sp.S == 1) c[r] = update_from(c[r], alpha, v);
+          else sp.part[q * m + r] = v;
+        }
+      }
+      cluster.sync();  // no CTA leaves before rank 0 has read its partial vector
+      if (lead && sp.S > 1) block_split_finish<T>(sp, 0, (int)q, 0, m < RT ? m : RT, c, alpha, red_d, &flag);
+    } else if (S > 1) {
       const int64_t t0 = rt * RT;
       block_split_finish<T>(sp, rt, s, t0, (m - t0 < RT) ? m - t0 : RT, c, alpha, red_d, &flag);
     }
   }
 }
 
+// Clusters of kColCluster CTAs of `kern` resident at once on the current
+// device (queried once per kernel and device).
+int cluster_capacity(const void* kern) {
+  struct Entry {
+    const void* k;
+    int dev, clusters;
+  };
+  static Entry cache[64];
+  static int used = 0;
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  for (int i = 0; i < used; ++i)
+    if (cache[i].k == kern && cache[i].dev == dev) return cache[i].clusters;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kColCluster * 1024);
+  cfg.blockDim = dim3(kThreads);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kColCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1) n = 1;
+  if (used < 64) cache[used++] = Entry{kern, dev, n};
+  return n;
+}
+
+// One CTA per column chunk in clusters of kColCluster.  The plan's chunk
+// count is capped here at the clusters the device runs at once (a second
+// wave would double the time): fewer, longer chunks, and as many cluster
+// partials as clusters (the workspace, sized for the plan's count, holds
+// them); FP32 chains past 64 products per thread take the LONG form.
+template <typename T, int V, int TX>
+int launch_cluster(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
+  constexpr int TY = kThreads / TX;
+  auto k0 = gemv_col_tile_kernel<T, V, TX, kColTileU, false, kColCluster>;
+  auto k1 = gemv_col_tile_kernel<T, V, TX, kColTileU, sizeof(T) == 4, kColCluster>;
+  int64_t parts = p.units / kColCluster;
+  const int cap = cluster_capacity((const void*)k0);
+  if (parts > cap) parts = cap;
+  const int64_t chunks = parts * kColCluster;
+  const int64_t kc = (a.n + chunks - 1) / chunks;
+  Split sp = p.split;
+  sp.S = sp.G = (int)parts;
+  sp.NG = 1;
+  const bool longc = sizeof(T) == 4 && (kc + TY - 1) / TY > 64;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)chunks);
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kColCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (longc)
+    cudaLaunchKernelEx(&cfg, k1, a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c, sp, kc, chunks);
+  else
+    cudaLaunchKernelEx(&cfg, k0, a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c, sp, kc, chunks);
+  return 0;
+}
+
 template <typename T, int V, int TX, bool LONG>
 int launch_tile(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
-  auto kern = gemv_col_tile_kernel<T, V, TX, kColTileU, LONG>;
+  if constexpr (TX * V <= 256) {
+    if (p.cluster == kColCluster) return launch_cluster<T, V, TX>(a, p, st);
+  }
+  auto kern = gemv_col_tile_kernel<T, V, TX, kColTileU, LONG, 0>;
   const int grid = grid_size((const void*)kern, p.units, 0, sizeof(T) == 8 ? kColTileWaves64 : 1);
   kern<<<grid, kThreads, 0, st>>>(a.m, a.n, a.alpha, a.A, a.lda, a.x, a.c, p.split, p.kc, p.units);
   return 0;
