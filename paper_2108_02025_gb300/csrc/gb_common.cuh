@@ -153,10 +153,12 @@ __device__ __forceinline__ void emu_fma(float ah, float al, float xh, float xl, 
 }
 
 // At most this many emulated products enter one FP32 pair before it is
-// folded into an FP64 sum (emu_fold).  With K products per pair, the pair's
-// rounding errors are at most u^2 (K(K+1)/2 - 1) + u (K+1) 1.25*2^-22 of the
-// sum of |a x| of its products (u = 2^-24); with the 2.5*2^-45 per product
-// of the operand cuts and of t, a chain of 16 is within 8.6e-13 of it.
+// folded into an FP64 sum (emu_fold).  With K products per pair and S the
+// sum of their |a x|, H + L differs from the sum of the products' p + t by
+// at most u^2 (K(K+1)/2 + 6K + 5) S (u = 2^-24: the TwoSum errors are below
+// u S each, L's two roundings per product below u|err + t| and u|L|); with
+// the 2.5*2^-45 per product of the operand cuts and of t, a chain of 16 is
+// within 9.2e-13 of S (a chain of 32 would be within 2.7e-12).
 constexpr int kEmuChain = 16;
 
 // FP64 value of an FP32 pair word by integer operations (no FP64
