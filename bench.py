@@ -1178,13 +1178,17 @@ def run_case(args):
     --scale k1,k2,... the long dimension (the larger of M and N; n for DOT)
     is multiplied by each factor in turn and t = t0 + bytes/bw is fitted
     over the median times, which separates a fixed cost per call from the
-    streaming bandwidth."""
+    streaming bandwidth.  host_us_per_call is the host's time to issue one
+    call; with --graph the rep's calls are replayed from one CUDA graph
+    instead, so that no host time can show between the kernels."""
     import torch
     import paper_2108_02025_gb300 as gb
     import synth
     op, dtype, layout, m0, n0 = args.case
     m0, n0 = int(m0), int(n0)
     device = torch.device("cuda", torch.cuda.current_device())
+    if args.graph:  # graphs are captured on a stream other than the default one
+        torch.cuda.set_stream(torch.cuda.Stream(device))
     stream = torch.cuda.current_stream(device)
     # L2 flush by reading a buffer of 4x the L2: a write would leave dirty
     # lines whose write-back overlaps the timed call
@@ -1246,13 +1250,26 @@ def run_case(args):
         for i in range(3 * copies):
             calls[i % copies]()
         torch.cuda.synchronize(device)
-        times = []
+        graph = None
+        if args.graph:  # the rep's calls captured once, on this stream's workspace
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                for i in range(args.batch):
+                    calls[i % copies]()
+            graph.replay()
+            torch.cuda.synchronize(device)
+        times, host = [], []
         for _ in range(args.reps):
             flush.sum()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for i in range(args.batch):
-                calls[i % copies]()
+            h0 = time.perf_counter()
+            if graph is not None:
+                graph.replay()
+            else:
+                for i in range(args.batch):
+                    calls[i % copies]()
+            host.append((time.perf_counter() - h0) / args.batch)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3 / args.batch)
@@ -1260,10 +1277,13 @@ def run_case(args):
         med = times[len(times) // 2]
         rows.append({"scale": k, "m": m, "n": n, "bytes": nb, "copies": copies,
                      "us_median": round(med * 1e6, 2), "us_min": round(times[0] * 1e6, 2),
+                     "host_us_per_call": round(statistics.median(host) * 1e6, 2),
                      "GB_s": round(nb / med / 1e9, 1), "frac_hbm": round(nb / med / 1e9 / hbm, 4)})
+        del graph
         del calls
         torch.cuda.empty_cache()
     out = {"case": [op, dtype, layout, m0, n0], "reps": args.reps, "calls_per_rep": args.batch,
+           "issue": "one CUDA graph of the rep's calls" if args.graph else "calls issued from the host",
            "l2": "flushed (512 MB read) before each rep; the calls of a rep take the operand copies in turn",
            "peak_gbs": hbm, "peak_source": src, "points": rows}
     if len(rows) >= 2:
@@ -1316,6 +1336,8 @@ def main(argv=None):
                    help="with --case: factors of the long dimension, e.g. 1,2,4,8, and a fit t = t0 + bytes/bw")
     p.add_argument("--reps", type=int, default=20, help="with --case: timed reps per size")
     p.add_argument("--batch", type=int, default=20, help="with --case: calls per rep, back to back")
+    p.add_argument("--graph", action="store_true",
+                   help="with --case: replay the rep's calls from one CUDA graph (no host issue time)")
     p.add_argument("--serve", type=int, default=None, metavar="REQUESTS",
                    help="serve one stream of this many requests through the engine alone")
     p.add_argument("--serve-rate", type=float, default=1e7, help="with --serve: arrivals per second")

@@ -32,7 +32,7 @@ constexpr int kRowLongB64 = 4;   // FP64 long-row kernel: resident blocks per SM
 // resident blocks per SM.
 constexpr int kRowMultiR = 2;
 constexpr int kRowMultiU = 4;
-constexpr int kRowMultiD = 1;
+constexpr int kRowMultiD = 0;
 constexpr int kRowMultiB = 4;
 constexpr int kRowMultiMinRows = 16;  // fewer FP64 rows take the one-row long kernel
 constexpr int kRowShortD64 = 2;  // FP64 short rows: of a lane's 8 packs, those on the FP64 pipe

@@ -332,7 +332,8 @@ __global__ void __launch_bounds__(kThreads, 4)
 }
 
 // FP64 long rows: a unit is a group of R consecutive rows times a chunk of
-// KC columns, so each 16-byte load of x, and each cut of an x value into
+// the columns (the pack rows s, s + S, ... of the rows, as in the long-row
+// kernel; KC is unused), so each 16-byte load of x, and each cut of an x value into
 // FP32 parts for the emulated products, serves R rows; per row the first D
 // of the U packs in flight go to the FP64 pipe (two chains), the rest to
 // emu_fma, voted per iteration as in the long-row kernel.  A group's missing
@@ -353,14 +354,13 @@ __global__ void __launch_bounds__(kThreads, kRowMultiB)
   __shared__ int flag;
 
   const int S = SPLIT ? sp.S : 1;
+  const int64_t PS = (int64_t)S * STEP;  // between a chunk's consecutive pack rows
+  const int64_t kv1 = (n / V) * V;       // the rows' whole packs
   const int64_t jlast = (int64_t)(31 - (threadIdx.x & 31)) * V;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {  // interleaved units
     const int64_t grp = SPLIT ? u / S : u;
     const int s = SPLIT ? (int)(u - grp * S) : 0;
     const int64_t row0 = grp * R;
-    const int64_t k0 = SPLIT ? (int64_t)s * KC : 0;
-    const int64_t k1 = SPLIT ? ((k0 + KC < n) ? k0 + KC : n) : n;
-    const int64_t kv1 = k0 + ((k1 - k0) / V) * V;
     const double* Ar[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) Ar[r] = A + (row0 + r < m ? row0 + r : m - 1) * lda;
@@ -372,16 +372,17 @@ __global__ void __launch_bounds__(kThreads, kRowMultiB)
       eh[r] = el[r] = 0.f;
     }
     int body = 0;
-    int64_t j = k0 + (int64_t)threadIdx.x * V;
+    // chunk s: the pack rows s, s + S, s + 2S, ... (as in the long-row kernel)
+    int64_t j = (int64_t)s * STEP + (int64_t)threadIdx.x * V;
 #pragma unroll 1
-    for (; j + jlast + (U - 1) * STEP < kv1; j += U * STEP) {
+    for (; j + jlast + (U - 1) * PS < kv1; j += U * PS) {
       Pack<double, V> xp[U], ap[R][U];
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int q = 0; q < U; ++q) ap[r][q] = ld_stream<double, V>(Ar[r] + j + q * STEP);
+        for (int q = 0; q < U; ++q) ap[r][q] = ld_stream<double, V>(Ar[r] + j + q * PS);
 #pragma unroll
-      for (int q = 0; q < U; ++q) xp[q] = ld_keep<double, V>(x + j + q * STEP);
+      for (int q = 0; q < U; ++q) xp[q] = ld_keep<double, V>(x + j + q * PS);
 #pragma unroll
       for (int q = 0; q < D; ++q)
 #pragma unroll
@@ -433,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, kRowMultiB)
       }
     }
 #pragma unroll 1
-    for (; j < kv1; j += STEP) {  // remaining whole packs, one at a time
+    for (; j < kv1; j += PS) {  // remaining whole packs, one at a time
       const Pack<double, V> xq = ld_keep<double, V>(x + j);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(kThreads, kRowMultiB)
         acc2[r] = __fma_rn(aq.v[1], xq.v[1], acc2[r]);
       }
     }
-    if (kv1 + threadIdx.x < k1) {  // ragged end (one column)
+    if (s == S - 1 && kv1 + threadIdx.x < n) {  // ragged end (one column), in the last chunk
       const int64_t jj = kv1 + threadIdx.x;
       const double xj = __ldg(x + jj);
 #pragma unroll
@@ -494,6 +495,7 @@ __global__ void __launch_bounds__(kThreads, PF ? kRowShortPfB : (sizeof(T) == 8 
   // FP64 columns
   constexpr int PD = sizeof(T) == 8 ? kRowShortD64 : PMAX;  // packs on the FP64 pipe
   __shared__ float2 xs[sizeof(T) == 8 ? 256 * V : 1];
+  bool xok = true;  // FP64: every x value of this lane's emulated packs is in range
   if constexpr (sizeof(T) == 8) {
     for (int64_t col = threadIdx.x; col < kv1; col += kThreads) {
       const double d = __ldg(x + col);
@@ -502,6 +504,15 @@ __global__ void __launch_bounds__(kThreads, PF ? kRowShortPfB : (sizeof(T) == 8 
       xs[col] = make_float2(h, lo);
     }
     __syncthreads();
+    // a lane's columns are the same in every row, so the x half of the
+    // range test is made once here
+#pragma unroll
+    for (int k = (sizeof(T) == 8 ? kRowShortD64 : PMAX); k < PMAX; ++k) {
+      const int64_t p = (int64_t)k * LPR + l;
+      if (p < packs)
+#pragma unroll
+        for (int v = 0; v < V; ++v) xok = xok && !isnan(xs[p * V + v].x);
+    }
   }
 
   // every thread runs the same number of iterations (the butterfly needs
@@ -556,20 +567,18 @@ __global__ void __launch_bounds__(kThreads, PF ? kRowShortPfB : (sizeof(T) == 8 
         }
       }
       // packs past the row or of a row past m take no part (they add 0)
-      unsigned rb = 0u;  // the emulated operands' ranges, OR-ed (x: its cut is NaN when out of range)
-      bool xbad = false;
+      unsigned rb = 0u;  // the emulated A operands' ranges, OR-ed (x: xok above)
 #pragma unroll
       for (int k = PD; k < PMAX; ++k) {
         const int64_t p = (int64_t)k * LPR + l;
         if (ok && p < packs) {
 #pragma unroll
-          for (int v = 0; v < V; ++v) {
-            rb |= emu_range(ap[k].v[v]);
-            xbad = xbad || isnan(xs[p * V + v].x);
-          }
+          for (int v = 0; v < V; ++v) rb |= emu_range(ap[k].v[v]);
         }
       }
-      if (__all_sync(__activemask(), rb < kEmuRange && !xbad)) {
+      // (a lane of a row past m votes with its x columns, which every row
+      // of the warp shares: the outcome is the one of the rows inside m)
+      if (__all_sync(__activemask(), rb < kEmuRange && xok)) {
         float eh = 0.f, el = 0.f;
 #pragma unroll
         for (int k = PD; k < PMAX; ++k) {
