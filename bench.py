@@ -489,6 +489,7 @@ def run_precision(device, stream, reps=20, sample_rows=64):
         times = []
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            gpu_lead(stream)
             e0.record(stream)
             call()
             e1.record(stream)
@@ -511,6 +512,7 @@ def run_precision(device, stream, reps=20, sample_rows=64):
             qt = []
             for _ in range(max(5, reps // 2)):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                gpu_lead(stream)
                 e0.record(stream)
                 qcall()
                 e1.record(stream)
@@ -577,11 +579,25 @@ class BatchWorkload:
         return a, self.x[self.x_off[p]:self.x_off[p] + n], self.c[self.c_off[p]:self.c_off[p] + m]
 
 
+LEAD_CYCLES = 1_000_000   # ~0.5 ms of GPU spin ahead of each timed region
+
+
+def gpu_lead(stream):
+    """Keep the GPU busy (a bounded spin kernel) while the host issues the
+    calls that a timed region starts with: otherwise the start event is
+    taken on an idle GPU, and the host's time to issue the first call (tens
+    of microseconds through ctypes) is counted as GPU time."""
+    import torch
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(LEAD_CYCLES)
+
+
 def _time_events(fn, stream, reps):
     import torch
     times = []
     for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        gpu_lead(stream)
         e0.record(stream)
         fn()
         e1.record(stream)
@@ -872,6 +888,7 @@ def run_ours(args):
     torch.cuda.synchronize(device)
     barrier()
     wall0 = time.time()
+    gpu_lead(stream)
     t_begin.record(stream)
     for k in range(args.steps):
         step(live_ev[k])
@@ -891,6 +908,7 @@ def run_ours(args):
         each = []
         for _ in range(OP_REPS):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            gpu_lead(stream)
             e0.record(stream)
             for _ in range(OP_CALLS):
                 wl.launch(op, sh)
@@ -898,6 +916,27 @@ def run_ours(args):
             e1.synchronize()
             each.append(e0.elapsed_time(e1) / 1e3 / OP_CALLS)
         per_op.append(sorted(each))
+    # The same OP_CALLS calls replayed from one CUDA graph: no host launch
+    # between the kernels, so the time per call is the device's alone
+    per_op_graph = []
+    cap = torch.cuda.Stream(device)
+    for op in ops:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap):
+            for _ in range(OP_CALLS):
+                wl.launch(op, cap.cuda_stream)
+        g.replay()
+        each = []
+        for _ in range(OP_REPS):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            gpu_lead(stream)
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            e1.synchronize()
+            each.append(e0.elapsed_time(e1) / 1e3 / OP_CALLS)
+        per_op_graph.append(statistics.mean(each))
+        del g
     clocks.stop()
 
     bytes_step = sum(alg_bytes(k, dt, m, n) for (_, k, dt, _, m, n) in ops)
@@ -914,7 +953,9 @@ def run_ours(args):
         ops_report.append({"op": name, "us": round(op_times[i] * 1e6, 2),
                            "us_median": round(each[len(each) // 2] * 1e6, 2), "us_min": round(each[0] * 1e6, 2),
                            "GB_s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4),
-                           "frac_nominal": round(gbs / NOMINAL_HBM_GBS, 4)})
+                           "frac_nominal": round(gbs / NOMINAL_HBM_GBS, 4),
+                           "us_graph": round(per_op_graph[i] * 1e6, 2),
+                           "frac_hbm_graph": round(alg_bytes(kind, dt, m, n) / per_op_graph[i] / 1e9 / hbm, 4)})
 
     e2e = None
     if not args.no_e2e:
@@ -973,7 +1014,9 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": len(ops) * args.steps,
             "ops_timing": f"after the timed steps, each operation {OP_CALLS} times back to back between two "
-                          f"CUDA events, {OP_REPS} such pairs; us = mean per call",
+                          f"CUDA events, {OP_REPS} such pairs; us = mean per call issued from the host, "
+                          f"us_graph = the same calls replayed from one CUDA graph (no host launch between "
+                          f"the kernels)",
             "clocks": clocks.summary(wall0, wall1),
             "ops": ops_report,
             "precision": precision,
@@ -1262,6 +1305,7 @@ def run_case(args):
         for _ in range(args.reps):
             flush.sum()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            gpu_lead(stream)
             e0.record(stream)
             h0 = time.perf_counter()
             if graph is not None:

@@ -76,6 +76,13 @@ __device__ __forceinline__ void cp_async_ca16(unsigned dst, const void* src) {
 __device__ __forceinline__ void cp_async_ca4(unsigned dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
 }
+// One element (4 or 8 bytes) through L1, for a value read long before use.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(sizeof(T))
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -238,21 +245,28 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
+// Counter increment with release and acquire semantics at GPU scope, one
+// instruction: the writes ordered before it (the caller's, and through a
+// barrier those of its block) are published with it, and the reads ordered
+// after it see what earlier arrivals published.  Returns the old value.
+__device__ __forceinline__ unsigned arrive_add(unsigned* ticket) {
+  unsigned prev;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(ticket) : "memory");
+  return prev;
+}
+
 // Arrival counter of one output tile.  Called by every thread of a block
 // after the block wrote its partial sums: returns true in the block that
 // arrived last (which then owns the final, fixed-order reduction).  The
-// fence/atomic pair publishes the partials of all earlier blocks to it.
+// barrier orders the block's partials before thread 0's counter increment
+// (release); in the last block the second barrier orders every thread's
+// reads of the other blocks' partials after it (acquire).  One thread
+// synchronises with the other blocks instead of every thread of the block.
 __device__ __forceinline__ bool arrive_last(unsigned* ticket, unsigned expected, int* flag) {
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned prev = atomicAdd(ticket, 1u);
-    *flag = (prev == expected - 1);
-  }
+  if (threadIdx.x == 0) *flag = arrive_add(ticket) == expected - 1;
   __syncthreads();
-  const bool last = *flag != 0;
-  if (last) __threadfence();
-  return last;
+  return *flag != 0;
 }
 
 // Sum over aligned groups of W lanes in the element type (FP32 partials
@@ -269,14 +283,12 @@ __device__ __forceinline__ float group_sum_f(float v) {
 // Returns true in the warp that arrived last; the fence/atomic pair makes
 // the partials of every earlier warp visible to it.
 __device__ __forceinline__ bool warp_arrive_last(unsigned* ticket, unsigned expected) {
-  __threadfence();
-  __syncwarp();
+  __syncwarp();  // orders the warp's partials before lane 0's increment (release)
   unsigned prev = 0;
-  if ((threadIdx.x & 31) == 0) prev = atomicAdd(ticket, 1u);
+  if ((threadIdx.x & 31) == 0) prev = arrive_add(ticket);
   prev = __shfl_sync(0xffffffffu, prev, 0);
-  const bool last = prev == expected - 1;
-  if (last) __threadfence();
-  return last;
+  __syncwarp();  // and the warp's later reads after it (acquire)
+  return prev == expected - 1;
 }
 
 // Warp-wide sum, for each of `rows` outputs, of `count` partials: value q
@@ -319,6 +331,8 @@ __device__ __forceinline__ void warp_sum_rows(const double* src, int64_t stride,
   else warp_sum_rows_p<1>(src, stride, count, row0, rows, sink);
 }
 
+constexpr int kSumBatch = 8;  // partial loads in flight per thread, block_sum_rows
+
 // Block-wide sum, for each of `rows` outputs, of `count` partials: value q
 // of row r is src[q * stride + row0 + r].  The 256 threads are cut into
 // slices of the partials so that all of them load at once: slice k adds its
@@ -340,14 +354,14 @@ __device__ void block_sum_rows(const double* src, int64_t stride, int count, int
       const int q0 = slice * per;
       const int q1 = q0 + per < count ? q0 + per : count;
       const double* p = src + row0 + r;
-      // up to eight loads in flight (the last batch predicated), then added
-      // in index order: one L2 round trip per eight partials
-      for (int q = q0; q < q1; q += 8) {
-        double v[8];
+      // up to kSumBatch loads in flight (the last batch predicated), then
+      // added in index order: one L2 round trip per kSumBatch partials
+      for (int q = q0; q < q1; q += kSumBatch) {
+        double v[kSumBatch];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = q + k < q1 ? __ldcg(p + (int64_t)(q + k) * stride) : 0.0;
+        for (int k = 0; k < kSumBatch; ++k) v[k] = q + k < q1 ? __ldcg(p + (int64_t)(q + k) * stride) : 0.0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < kSumBatch; ++k)
           if (q + k < q1) acc = __dadd_rn(acc, v[k]);
       }
     }
@@ -367,9 +381,13 @@ __device__ void block_sum_rows(const double* src, int64_t stride, int count, int
 // rows [row0, row0 + rows) of tile `tile` (called by every thread).  The
 // last block of each group of sp.G splits sums the group, the last group
 // sums the groups and applies c <- c + alpha*sum; counters return to zero.
+// cpre, when given (shared memory), holds c[row0 .. row0 + rows) read
+// earlier, so that the final update waits on no load of c.
 template <typename T>
 __device__ __noinline__ void block_split_finish(const Split& sp, int64_t tile, int s, int64_t row0,
-                                                int64_t rows, T* c, T alpha, double* red, int* flag) {
+                                                int64_t rows, T* c, T alpha, double* red, int* flag,
+                                                const T* cpre = nullptr) {
+  auto c0 = [&](int64_t row) { return cpre ? cpre[row - row0] : c[row]; };
   const int g = s / sp.G;
   const int gsize = (g + 1) * sp.G <= sp.S ? sp.G : sp.S - g * sp.G;
   unsigned* t1 = sp.tickets + tile * (sp.NG + 1) + g;
@@ -378,7 +396,7 @@ __device__ __noinline__ void block_split_finish(const Split& sp, int64_t tile, i
   const double* src = sp.part + (int64_t)g * sp.G * sp.m;
   if (sp.NG == 1) {
     block_sum_rows(src, sp.m, gsize, row0, rows, red,
-                   [&](int64_t row, double v) { c[row] = update_from(c[row], alpha, v); });
+                   [&](int64_t row, double v) { c[row] = update_from(c0(row), alpha, v); });
     if (threadIdx.x == 0) *t1 = 0u;
     return;
   }
@@ -387,7 +405,7 @@ __device__ __noinline__ void block_split_finish(const Split& sp, int64_t tile, i
   if (threadIdx.x == 0) *t1 = 0u;
   if (!arrive_last(t2, (unsigned)sp.NG, flag)) return;
   block_sum_rows(sp.part2, sp.m, sp.NG, row0, rows, red,
-                 [&](int64_t row, double v) { c[row] = update_from(c[row], alpha, v); });
+                 [&](int64_t row, double v) { c[row] = update_from(c0(row), alpha, v); });
   if (threadIdx.x == 0) *t2 = 0u;
 }
 

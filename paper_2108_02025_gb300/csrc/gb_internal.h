@@ -27,6 +27,7 @@ constexpr int kRowLongU = 4;     // packs in flight per thread, long-row kernel 
 constexpr int kRowLongU64 = 8;   // the same for FP64
 constexpr int kRowLongD64 = 4;   // of those, packs formed on the FP64 pipe (the rest emulated)
 constexpr int kRowLongB64 = 4;   // FP64 long-row kernel: resident blocks per SM budgeted for
+constexpr int kRowHeld = 4;      // split long rows: units per block whose arrival waits for the block's end
 // FP64 long rows (at least kRowMultiMinRows): R rows per unit share each load
 // and cut of x; U packs per row in flight, D of them on the FP64 pipe; B
 // resident blocks per SM.
@@ -51,6 +52,7 @@ constexpr int kColTileD64Short = 2;  // the same for tiles of 128 or more rows (
 // CTAs per thread-block cluster (partials summed in distributed shared
 // memory, one partial per cluster left for the final sum).
 constexpr int kColCluster = 8;
+constexpr int kColClusterU32 = 12;  // FP32: columns in flight per thread in that launch
 constexpr int64_t kColShortN = 512;  // column-major: n up to this takes tiles of up to 256 row threads
 constexpr int64_t kColMinUnits = 1;  // column-major: split until at least this many units per block
 constexpr int64_t kRowMinUnits = 2;  // row-major long rows: the same

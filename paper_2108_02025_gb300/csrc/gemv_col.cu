@@ -179,12 +179,21 @@ __global__ void __launch_bounds__(kThreads, 4)
   __shared__ T redT[kThreads * V];
   __shared__ double red_d[kThreads];
   __shared__ double cpart[CL > 0 ? TX * V : 1];  // CL: this CTA's partial vector
+  __shared__ T cpre[CL > 0 ? TX * V : 1];         // CL: c of the tile's rows
   __shared__ int flag;
 
   const int tx = threadIdx.x % TX;
   const int ty = threadIdx.x / TX;
   const int S = CL > 0 ? (int)units : sp.S;  // column chunks per row tile
   const int64_t cstep = (int64_t)TY * lda;  // between a thread's columns
+
+  // CL: c of the tile's rows (one per thread) copied into shared memory
+  // while the columns stream, so that the final update waits on no load of c
+  if constexpr (CL > 0) {
+    static_assert(TX * V <= kThreads, "a cluster tile has at most one row per thread");
+    if (threadIdx.x < RT && threadIdx.x < m) cp_async_elem(&cpre[threadIdx.x], c + threadIdx.x);
+    cp_async_commit();
+  }
 
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {  // interleaved units
     const int64_t rt = u / S;
@@ -335,6 +344,7 @@ __global__ void __launch_bounds__(kThreads, 4)
     if constexpr (CL > 0) {
       namespace cg = cooperative_groups;
       cg::cluster_group cluster = cg::this_cluster();
+      cp_async_wait<0>();  // this thread's row of cpre (read only by this thread or after a barrier)
       cluster.sync();  // every CTA of the cluster holds its partial vector
       const bool lead = cluster.block_rank() == 0;
       const int64_t q = blockIdx.x / CL;  // the cluster's partial
@@ -343,12 +353,12 @@ __global__ void __launch_bounds__(kThreads, 4)
           double v = 0.0;
 #pragma unroll
           for (int k = 0; k < CL; ++k) v = __dadd_rn(v, *cluster.map_shared_rank(&cpart[r], k));
-          if (sp.S == 1) c[r] = update_from(c[r], alpha, v);
+          if (sp.S == 1) c[r] = update_from(cpre[r], alpha, v);
           else sp.part[q * m + r] = v;
         }
       }
       cluster.sync();  // no CTA leaves before rank 0 has read its partial vector
-      if (lead && sp.S > 1) block_split_finish<T>(sp, 0, (int)q, 0, m < RT ? m : RT, c, alpha, red_d, &flag);
+      if (lead && sp.S > 1) block_split_finish<T>(sp, 0, (int)q, 0, m < RT ? m : RT, c, alpha, red_d, &flag, cpre);
     } else if (S > 1) {
       const int64_t t0 = rt * RT;
       block_split_finish<T>(sp, rt, s, t0, (m - t0 < RT) ? m - t0 : RT, c, alpha, red_d, &flag);
@@ -395,8 +405,9 @@ int cluster_capacity(const void* kern) {
 template <typename T, int V, int TX>
 int launch_cluster(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
   constexpr int TY = kThreads / TX;
-  auto k0 = gemv_col_tile_kernel<T, V, TX, kColTileU, false, kColCluster>;
-  auto k1 = gemv_col_tile_kernel<T, V, TX, kColTileU, sizeof(T) == 4, kColCluster>;
+  constexpr int U = sizeof(T) == 4 ? kColClusterU32 : kColTileU;
+  auto k0 = gemv_col_tile_kernel<T, V, TX, U, false, kColCluster>;
+  auto k1 = gemv_col_tile_kernel<T, V, TX, U, sizeof(T) == 4, kColCluster>;
   int64_t parts = p.units / kColCluster;
   const int cap = cluster_capacity((const void*)k0);
   if (parts > cap) parts = cap;

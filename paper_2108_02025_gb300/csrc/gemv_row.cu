@@ -52,6 +52,23 @@ __device__ __forceinline__ T block_total(T v, T* red) {
   return t;
 }
 
+// The final step of a split row, in the block that arrived last: the S
+// chunk partials in FP64 (thread t adds chunks t, t+256, ... in order, then
+// the fixed block order), c_row <- c0 + alpha * sum (c0, the row's c, is
+// read in thread 0 only), and the row's counter back to zero.  Every thread
+// of the block calls it.
+template <typename T>
+__device__ __forceinline__ void row_split_sum(const Split& sp, int64_t row, int S, T alpha, T* c, double c0,
+                                              double* red_d) {
+  double p = 0.0;
+  for (int q = threadIdx.x; q < S; q += kThreads) p = __dadd_rn(p, __ldcg(sp.part + (int64_t)q * sp.m + row));
+  const double sum = block_total<double>(p, red_d);
+  if (threadIdx.x == 0) {
+    c[row] = update_from((T)c0, alpha, sum);  // c0 holds a T exactly
+    sp.tickets[row] = 0u;
+  }
+}
+
 // Long rows.  unit u = (row u / S, chunk u % S).
 template <typename T, int V, int U, bool LONG>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowLongB64 : 4)
@@ -66,9 +83,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowLongB64 : 4)
   constexpr int EFLUSH = (U - UD) * V > 0 && kEmuChain / ((U - UD) * V) > 0 ? kEmuChain / ((U - UD) * V) : 1;
   __shared__ double red_d[kThreads / 32];
   __shared__ int flag;
+  // split rows: the block's first kRowHeld units have their arrival deferred
+  // to the end of the block's work (row, prefetched c, and whether this
+  // block finishes the row), so that no block stops streaming mid-kernel to
+  // finish a row
+  __shared__ int64_t hrow[kRowHeld];
+  __shared__ double hc[kRowHeld];
+  __shared__ int hlast[kRowHeld];
   T* red = reinterpret_cast<T*>(red_d);
 
   const int S = sp.S;
+  int nheld = 0;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {  // interleaved units
     const int64_t row = u / S;
     const int s = (int)(u - row * S);
@@ -76,6 +101,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowLongB64 : 4)
     const int64_t k1 = (k0 + KC < n) ? k0 + KC : n;
     const int64_t kv1 = k0 + ((k1 - k0) / V) * V;
     const T* Ar = A + row * lda;
+    // split rows: c of the row, read now so that a final update waits on no load
+    T c0 = T(0);
+    if (S > 1 && threadIdx.x == 0) c0 = c[row];
 
     T acc = T(0), acc2 = T(0), hi = T(0), lo = T(0);
     float eh = 0.f, el = 0.f;  // FP64: the pair of the FP32-emulated products
@@ -171,18 +199,23 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowLongB64 : 4)
       if (threadIdx.x == 0) c[row] = update(c[row], alpha, total);
     } else {
       if (threadIdx.x == 0) sp.part[(int64_t)s * m + row] = (double)total;
-      if (arrive_last(sp.tickets + row, (unsigned)S, &flag)) {
-        // the row's S chunk partials in FP64: thread t adds chunks t, t+256,
-        // ... in order, then the fixed block order
-        double p = 0.0;
-        for (int q = threadIdx.x; q < S; q += kThreads) p = __dadd_rn(p, __ldcg(sp.part + (int64_t)q * m + row));
-        const double sum = block_total<double>(p, red_d);
+      if (nheld < kRowHeld) {  // arrival deferred (block-uniform count)
         if (threadIdx.x == 0) {
-          c[row] = update_from(c[row], alpha, sum);
-          sp.tickets[row] = 0u;
+          hrow[nheld] = row;
+          hc[nheld] = (double)c0;
         }
+        ++nheld;
+      } else if (arrive_last(sp.tickets + row, (unsigned)S, &flag)) {
+        row_split_sum(sp, row, S, alpha, c, (double)c0, red_d);  // (c0 is read in thread 0 only)
       }
     }
+  }
+  if (nheld > 0) {  // the deferred arrivals, all at once: thread k arrives for entry k
+    __syncthreads();  // the partials and the entries are written
+    if (threadIdx.x < nheld) hlast[threadIdx.x] = arrive_add(sp.tickets + hrow[threadIdx.x]) == (unsigned)S - 1;
+    __syncthreads();  // the last arrival's partial reads come after its increment
+    for (int k = 0; k < nheld; ++k)
+      if (hlast[k]) row_split_sum(sp, hrow[k], S, alpha, c, hc[k], red_d);
   }
 }
 
