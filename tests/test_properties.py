@@ -73,7 +73,9 @@ def test_engine_host_only_invariants(reqs, budget_mb, streams, max_inflight, max
     chunks: every accepted request completes once, the budget and the caps
     hold, admission follows arrival order."""
     budget = budget_mb << 20
-    P = 1 << 23
+    # a pool holds every operand drawn here (m, n <= 3000, rows padded to
+    # 16 bytes): a longer operand is refused by design (gbserve.h)
+    P = 1 << 24
     with gb.Engine(budget, streams=streams, max_inflight=max_inflight, max_step_requests=max_step,
                    host_only=True, sim_bytes_per_ns=500.0, pool_elems=P, chunk_bytes=chunk) as e:
         t0 = e.now_ns() + 2_000_000
