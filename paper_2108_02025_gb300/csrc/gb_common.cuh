@@ -245,6 +245,9 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
+// Release/acquire fence at GPU scope.
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 // Counter increment with release and acquire semantics at GPU scope, one
 // instruction: the writes ordered before it (the caller's, and through a
 // barrier those of its block) are published with it, and the reads ordered
@@ -381,13 +384,9 @@ __device__ void block_sum_rows(const double* src, int64_t stride, int count, int
 // rows [row0, row0 + rows) of tile `tile` (called by every thread).  The
 // last block of each group of sp.G splits sums the group, the last group
 // sums the groups and applies c <- c + alpha*sum; counters return to zero.
-// cpre, when given (shared memory), holds c[row0 .. row0 + rows) read
-// earlier, so that the final update waits on no load of c.
 template <typename T>
 __device__ __noinline__ void block_split_finish(const Split& sp, int64_t tile, int s, int64_t row0,
-                                                int64_t rows, T* c, T alpha, double* red, int* flag,
-                                                const T* cpre = nullptr) {
-  auto c0 = [&](int64_t row) { return cpre ? cpre[row - row0] : c[row]; };
+                                                int64_t rows, T* c, T alpha, double* red, int* flag) {
   const int g = s / sp.G;
   const int gsize = (g + 1) * sp.G <= sp.S ? sp.G : sp.S - g * sp.G;
   unsigned* t1 = sp.tickets + tile * (sp.NG + 1) + g;
@@ -396,7 +395,7 @@ __device__ __noinline__ void block_split_finish(const Split& sp, int64_t tile, i
   const double* src = sp.part + (int64_t)g * sp.G * sp.m;
   if (sp.NG == 1) {
     block_sum_rows(src, sp.m, gsize, row0, rows, red,
-                   [&](int64_t row, double v) { c[row] = update_from(c0(row), alpha, v); });
+                   [&](int64_t row, double v) { c[row] = update_from(c[row], alpha, v); });
     if (threadIdx.x == 0) *t1 = 0u;
     return;
   }
@@ -405,7 +404,7 @@ __device__ __noinline__ void block_split_finish(const Split& sp, int64_t tile, i
   if (threadIdx.x == 0) *t1 = 0u;
   if (!arrive_last(t2, (unsigned)sp.NG, flag)) return;
   block_sum_rows(sp.part2, sp.m, sp.NG, row0, rows, red,
-                 [&](int64_t row, double v) { c[row] = update_from(c0(row), alpha, v); });
+                 [&](int64_t row, double v) { c[row] = update_from(c[row], alpha, v); });
   if (threadIdx.x == 0) *t2 = 0u;
 }
 

@@ -147,6 +147,44 @@ __global__ void __launch_bounds__(kThreads, 3)
   }
 }
 
+// The last cluster's sum of the S cluster partials of rows [0, rows): CTA
+// `rank` takes the rows rank*RPC .. rank*RPC + RPC - 1 (RPC = rows / CL,
+// rounded up); for each, NS = 256 / RPC slices of the partials are summed
+// in index order (slice j: partials j*per .. j*per + per - 1, loads issued
+// together), then the slices in slice order, and c <- c0 + alpha * sum.
+// Every thread of the CTA calls it.
+template <typename T, int CL>
+__device__ __noinline__ void cluster_final_sum(const Split& sp, int rank, int rows, T* c, T alpha,
+                                               const T* cpre, double* red) {
+  const int rpc = (rows + CL - 1) / CL;
+  const int r0 = rank * rpc;
+  const int nr = r0 + rpc <= rows ? rpc : (rows > r0 ? rows - r0 : 0);
+  if (nr <= 0) return;
+  const int ns = kThreads / rpc;
+  const int per = (sp.S + ns - 1) / ns;
+  const int r = threadIdx.x % rpc, j = threadIdx.x / rpc;
+  double acc = 0.0;
+  if (j < ns && r < nr) {
+    const int q0 = j * per, q1 = q0 + per < sp.S ? q0 + per : sp.S;
+    const double* p = sp.part + r0 + r;
+    for (int qb = q0; qb < q1; qb += 8) {
+      double v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = qb + k < q1 ? __ldcg(p + (int64_t)(qb + k) * sp.m) : 0.0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (qb + k < q1) acc = __dadd_rn(acc, v[k]);
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < nr) {
+    double t = 0.0;
+    for (int k = 0; k < ns; ++k) t = __dadd_rn(t, red[k * rpc + threadIdx.x]);
+    c[r0 + threadIdx.x] = update_from(cpre[r0 + threadIdx.x], alpha, t);
+  }
+}
+
 // 16-byte aligned operands: block tiles.  A work unit is a tile of RT = TX*V
 // rows by a chunk of KC columns; thread (tx, ty) owns rows tx*V .. tx*V+V-1
 // of the tile (one 16-byte pack per column) and every TY-th column of the
@@ -356,9 +394,26 @@ __global__ void __launch_bounds__(kThreads, 4)
           if (sp.S == 1) c[r] = update_from(cpre[r], alpha, v);
           else sp.part[q * m + r] = v;
         }
+        if (sp.S > 1) {
+          // the cluster's arrival, told to every CTA of the cluster
+          __syncthreads();  // the cluster partial is written (released by the increment)
+          if (threadIdx.x == 0) {
+            const int last = arrive_add(sp.tickets) == (unsigned)sp.S - 1;
+#pragma unroll
+            for (int k = 0; k < CL; ++k) *cluster.map_shared_rank(&flag, k) = last;
+            if (last) *sp.tickets = 0u;  // every cluster has arrived
+          }
+        }
       }
-      cluster.sync();  // no CTA leaves before rank 0 has read its partial vector
-      if (lead && sp.S > 1) block_split_finish<T>(sp, 0, (int)q, 0, m < RT ? m : RT, c, alpha, red_d, &flag, cpre);
+      // rank 0 has read every partial vector and written every flag; no CTA
+      // leaves before that
+      cluster.sync();
+      if (sp.S > 1 && flag) {
+        // the last cluster: CTA k sums the cluster partials of its share of
+        // the rows, all of its loads in one round trip
+        fence_acq_rel_gpu();  // (the cluster barrier carries rank 0's acquire; made explicit)
+        cluster_final_sum<T, CL>(sp, (int)cluster.block_rank(), m < RT ? (int)m : RT, c, alpha, cpre, red_d);
+      }
     } else if (S > 1) {
       const int64_t t0 = rt * RT;
       block_split_finish<T>(sp, rt, s, t0, (m - t0 < RT) ? m - t0 : RT, c, alpha, red_d, &flag);
@@ -401,7 +456,8 @@ int cluster_capacity(const void* kern) {
 // count is capped here at the clusters the device runs at once (a second
 // wave would double the time): fewer, longer chunks, and as many cluster
 // partials as clusters (the workspace, sized for the plan's count, holds
-// them); FP32 chains past 64 products per thread take the LONG form.
+// them); FP32 chains past 64 products per thread take the LONG form.  The
+// last cluster to arrive sums the cluster partials with all of its CTAs.
 template <typename T, int V, int TX>
 int launch_cluster(const GemvArgs<T>& a, const GemvPlan& p, cudaStream_t st) {
   constexpr int TY = kThreads / TX;
