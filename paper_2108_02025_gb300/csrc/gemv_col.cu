@@ -149,9 +149,10 @@ __global__ void __launch_bounds__(kThreads, 3)
 
 // The last cluster's sum of the S cluster partials of rows [0, rows): CTA
 // `rank` takes the rows rank*RPC .. rank*RPC + RPC - 1 (RPC = rows / CL,
-// rounded up); for each, NS = 256 / RPC slices of the partials are summed
-// in index order (slice j: partials j*per .. j*per + per - 1, loads issued
-// together), then the slices in slice order, and c <- c0 + alpha * sum.
+// rounded up); for each, NS = min(256 / RPC, 32) slices of the partials
+// are summed in index order (slice j: partials j*per .. j*per + per - 1,
+// loads issued together), then the slices in slice order, and
+// c <- c0 + alpha * sum.
 // Every thread of the CTA calls it.
 template <typename T, int CL>
 __device__ __noinline__ void cluster_final_sum(const Split& sp, int rank, int rows, T* c, T alpha,
@@ -160,7 +161,8 @@ __device__ __noinline__ void cluster_final_sum(const Split& sp, int rank, int ro
   const int r0 = rank * rpc;
   const int nr = r0 + rpc <= rows ? rpc : (rows > r0 ? rows - r0 : 0);
   if (nr <= 0) return;
-  const int ns = kThreads / rpc;
+  int ns = kThreads / rpc;  // slices per row, at most 32 (their sum is sequential)
+  if (ns > 32) ns = 32;
   const int per = (sp.S + ns - 1) / ns;
   const int r = threadIdx.x % rpc, j = threadIdx.x / rpc;
   double acc = 0.0;
