@@ -62,6 +62,7 @@ constexpr int64_t kRowMinUnits = 2;  // row-major long rows: the same
 constexpr int kQuantRows[2] = {4, 4};
 constexpr int kQuantPacks[2] = {2, 1};
 constexpr int kQuantMinBlocks[2] = {2, 3};
+constexpr int kQuantE4M3U = 8;  // E4M3 quantiser: 16-byte packs in flight per thread
 
 // How one GEMV is cut into work.  The kernel, the split S and the per-thread
 // summation order depend only on (dtype, layout, m, n) and on the pointer

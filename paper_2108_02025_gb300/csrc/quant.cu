@@ -105,11 +105,23 @@ __global__ void __launch_bounds__(kThreads)
     const float* Ar = A + i * lda;
     uint8_t* Qr = Q + i * ldq;
     float amax = 0.f;
-    for (int64_t j = (int64_t)threadIdx.x * 4; j < nv; j += (int64_t)kThreads * 4) {
+    // kQuantE4M3U packs of 16 bytes in flight per thread, then one at a time
+    constexpr int QU = kQuantE4M3U;
+    constexpr int64_t QS = (int64_t)kThreads * 4;  // columns per pack row
+    int64_t j = (int64_t)threadIdx.x * 4;
+    for (; j + (QU - 1) * QS < nv; j += QU * QS) {
+      float4 a[QU];
+#pragma unroll
+      for (int q = 0; q < QU; ++q) a[q] = __ldcg(reinterpret_cast<const float4*>(Ar + j + q * QS));
+#pragma unroll
+      for (int q = 0; q < QU; ++q)
+        amax = fmaxf(amax, fmaxf(fmaxf(fabsf(a[q].x), fabsf(a[q].y)), fmaxf(fabsf(a[q].z), fabsf(a[q].w))));
+    }
+    for (; j < nv; j += QS) {
       const float4 a = __ldcg(reinterpret_cast<const float4*>(Ar + j));
       amax = fmaxf(amax, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))));
     }
-    for (int64_t j = nv + threadIdx.x; j < n; j += kThreads) amax = fmaxf(amax, fabsf(__ldcg(Ar + j)));
+    for (int64_t jj = nv + threadIdx.x; jj < n; jj += kThreads) amax = fmaxf(amax, fabsf(__ldcg(Ar + jj)));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     __syncthreads();
@@ -123,11 +135,21 @@ __global__ void __launch_bounds__(kThreads)
     auto code = [&](float v) -> unsigned {
       return s != 0.f ? (unsigned)__nv_cvt_float_to_fp8(__fdiv_rn(v, s), __NV_SATFINITE, __NV_E4M3) : 0u;
     };
-    for (int64_t j = (int64_t)threadIdx.x * 4; j < nv; j += (int64_t)kThreads * 4) {
+    j = (int64_t)threadIdx.x * 4;
+    for (; j + (QU - 1) * QS < nv; j += QU * QS) {
+      float4 a[QU];
+#pragma unroll
+      for (int q = 0; q < QU; ++q) a[q] = __ldcs(reinterpret_cast<const float4*>(Ar + j + q * QS));
+#pragma unroll
+      for (int q = 0; q < QU; ++q)
+        *reinterpret_cast<unsigned*>(Qr + j + q * QS) =
+            code(a[q].x) | (code(a[q].y) << 8) | (code(a[q].z) << 16) | (code(a[q].w) << 24);
+    }
+    for (; j < nv; j += QS) {
       const float4 a = __ldcs(reinterpret_cast<const float4*>(Ar + j));
       *reinterpret_cast<unsigned*>(Qr + j) = code(a.x) | (code(a.y) << 8) | (code(a.z) << 16) | (code(a.w) << 24);
     }
-    for (int64_t j = nv + threadIdx.x; j < n; j += kThreads) Qr[j] = (uint8_t)code(__ldcs(Ar + j));
+    for (int64_t jj = nv + threadIdx.x; jj < n; jj += kThreads) Qr[jj] = (uint8_t)code(__ldcs(Ar + jj));
   }
 }
 
