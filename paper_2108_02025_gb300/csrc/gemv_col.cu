@@ -215,7 +215,8 @@ __global__ void __launch_bounds__(kThreads, 4)
   // FP64: columns on the FP64 pipe per iteration (tiles of 128 or more rows
   // occur only with few columns, where more emulation measured faster)
   constexpr int DU = sizeof(T) == 8 ? (TX >= 128 ? kColTileD64Short : kColTileD64) : U;
-  constexpr int EFLUSH = U > DU && kEmuChain / (U - DU) > 0 ? kEmuChain / (U - DU) : 1;
+  constexpr int NEM = U > DU ? U - DU : 1;  // emulated columns per iteration (1 when none)
+  constexpr int EFLUSH = kEmuChain / NEM > 0 ? kEmuChain / NEM : 1;
   __shared__ T redT[kThreads * V];
   __shared__ double red_d[kThreads];
   __shared__ double cpart[CL > 0 ? TX * V : 1];  // CL: this CTA's partial vector

@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? kRowLongB64 : 4)
   // FLUSH bodies it is folded into a compensated FP32 sum (TwoSum)
   constexpr int FLUSH = LONG ? (64 / (U * V) > 0 ? 64 / (U * V) : 1) : 1 << 30;
   constexpr int UD = sizeof(T) == 8 ? (kRowLongD64 < U ? kRowLongD64 : U) : U;  // packs on the FP64 pipe
-  constexpr int EFLUSH = (U - UD) * V > 0 && kEmuChain / ((U - UD) * V) > 0 ? kEmuChain / ((U - UD) * V) : 1;
+  constexpr int NEM = (U - UD) * V > 0 ? (U - UD) * V : 1;  // emulated products per iteration (1 when none)
+  constexpr int EFLUSH = kEmuChain / NEM > 0 ? kEmuChain / NEM : 1;
   __shared__ double red_d[kThreads / 32];
   __shared__ int flag;
   // split rows: the block's first kRowHeld units have their arrival deferred
