@@ -149,11 +149,11 @@ __global__ void __launch_bounds__(kThreads, 3)
 
 // The last cluster's sum of the S cluster partials of rows [0, rows): CTA
 // `rank` takes the rows rank*RPC .. rank*RPC + RPC - 1 (RPC = rows / CL,
-// rounded up); for each, NS = min(256 / RPC, 32) slices of the partials
-// are summed in index order (slice j: partials j*per .. j*per + per - 1,
-// loads issued together), then the slices in slice order, and
-// c <- c0 + alpha * sum.
-// Every thread of the CTA calls it.
+// rounded up); thread t works on row t % P of them (P = RPC rounded up to
+// a power of two, at most 32) and on slice t / P of the partials, which it
+// sums in index order (loads issued together); the 32 / P slices of a row
+// in a warp are added by a fixed xor butterfly, the 8 warps' sums in warp
+// order, and c <- c0 + alpha * sum.  Every thread of the CTA calls it.
 template <typename T, int CL>
 __device__ __noinline__ void cluster_final_sum(const Split& sp, int rank, int rows, T* c, T alpha,
                                                const T* cpre, double* red) {
@@ -161,12 +161,13 @@ __device__ __noinline__ void cluster_final_sum(const Split& sp, int rank, int ro
   const int r0 = rank * rpc;
   const int nr = r0 + rpc <= rows ? rpc : (rows > r0 ? rows - r0 : 0);
   if (nr <= 0) return;
-  int ns = kThreads / rpc;  // slices per row, at most 32 (their sum is sequential)
-  if (ns > 32) ns = 32;
+  int p2 = 1;
+  while (p2 < rpc) p2 <<= 1;
+  const int ns = kThreads / p2;  // slices per row
   const int per = (sp.S + ns - 1) / ns;
-  const int r = threadIdx.x % rpc, j = threadIdx.x / rpc;
+  const int r = threadIdx.x % p2, j = threadIdx.x / p2;
   double acc = 0.0;
-  if (j < ns && r < nr) {
+  if (r < nr) {
     const int q0 = j * per, q1 = q0 + per < sp.S ? q0 + per : sp.S;
     const double* p = sp.part + r0 + r;
     for (int qb = q0; qb < q1; qb += 8) {
@@ -178,11 +179,14 @@ __device__ __noinline__ void cluster_final_sum(const Split& sp, int rank, int ro
         if (qb + k < q1) acc = __dadd_rn(acc, v[k]);
     }
   }
-  red[threadIdx.x] = acc;
+  for (int o = 16; o >= p2; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+  const int lane = threadIdx.x & 31;
+  if (lane < p2) red[(threadIdx.x >> 5) * p2 + lane] = acc;
   __syncthreads();
   if (threadIdx.x < nr) {
     double t = 0.0;
-    for (int k = 0; k < ns; ++k) t = __dadd_rn(t, red[k * rpc + threadIdx.x]);
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) t = __dadd_rn(t, red[w * p2 + threadIdx.x]);
     c[r0 + threadIdx.x] = update_from(cpre[r0 + threadIdx.x], alpha, t);
   }
 }
@@ -367,13 +371,28 @@ __global__ void __launch_bounds__(kThreads, 4)
       for (int v = 0; v < V; ++v) emu_fold(acc[v], eh[v], el[v]);
     }
 
+    // CL (TX < 32): the 32 / TX column lanes of a warp are first added by a
+    // fixed xor butterfly, so that the shared-memory sum has one entry per
+    // warp and row instead of one per column lane
+    constexpr bool WB = CL > 0 && TX < 32;
+    constexpr int NY = WB ? kThreads / 32 : TY;  // entries per row in redT
     __syncthreads();  // redT is free
+    if constexpr (WB) {
 #pragma unroll
-    for (int v = 0; v < V; ++v) redT[ty * RT + tx * V + v] = acc[v];
+      for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int o = 16; o >= TX; o >>= 1) acc[v] = acc[v] + __shfl_xor_sync(0xffffffffu, acc[v], o);
+      if ((threadIdx.x & 31) < TX)
+#pragma unroll
+        for (int v = 0; v < V; ++v) redT[(threadIdx.x >> 5) * RT + tx * V + v] = acc[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) redT[ty * RT + tx * V + v] = acc[v];
+    }
     __syncthreads();
     for (int r = threadIdx.x; r < RT; r += kThreads) {
       T t = T(0);
-      for (int y = 0; y < TY; ++y) t = t + redT[y * RT + r];
+      for (int y = 0; y < NY; ++y) t = t + redT[y * RT + r];
       const int64_t row = rt * RT + r;
       if constexpr (CL > 0) {
         cpart[r] = (double)t;
