@@ -37,7 +37,7 @@ constexpr int kRowMultiD = 0;
 constexpr int kRowMultiB = 4;
 constexpr int kRowMultiMinRows = 16;  // fewer FP64 rows take the one-row long kernel
 constexpr int kRowShortD64 = 2;  // FP64 short rows: of a lane's 8 packs, those on the FP64 pipe
-constexpr int kRowShortB64 = 4;  // FP64 short rows: resident blocks per SM budgeted for
+constexpr int kRowShortB64 = 3;  // FP64 short rows: resident blocks per SM budgeted for
 // Short rows: the next row block's packs loaded while the current one is
 // summed (FP64, FP32), and the resident blocks per SM budgeted for then.
 constexpr bool kRowShortPf64 = false;
@@ -52,7 +52,7 @@ constexpr int kColTileD64Short = 2;  // the same for tiles of 128 or more rows (
 // CTAs per thread-block cluster (partials summed in distributed shared
 // memory, one partial per cluster left for the final sum).
 constexpr int kColCluster = 8;
-constexpr int kColClusterU32 = 12;  // FP32: columns in flight per thread in that launch
+constexpr int kColClusterU32 = 10;  // FP32: columns in flight per thread in that launch
 constexpr int64_t kColShortN = 512;  // column-major: n up to this takes tiles of up to 256 row threads
 constexpr int64_t kColMinUnits = 1;  // column-major: split until at least this many units per block
 constexpr int64_t kRowMinUnits = 2;  // row-major long rows: the same
