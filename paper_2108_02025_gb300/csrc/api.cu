@@ -255,8 +255,12 @@ inline ColShape col_shape(size_t e, bool vec, int64_t m, int64_t n) {
   if (vec) {  // block tiles of tx*V rows; tx threads along the rows, 256/tx along the columns
     // short columns (n small): up to all 256 threads along the rows, no
     // cross-lane sum (FP64: up to 128, so that a tile is smaller and the
-    // last wave of tiles shorter); otherwise at most 64
-    const int64_t tx = pow2_at_least(cdiv(m, V), n <= kColShortN ? (e == 8 ? 128 : 256) : 64);
+    // last wave of tiles shorter, unless n <= 32, where two column lanes
+    // would leave each thread too few columns for its fixed cost per tile:
+    // 2097152x32 102.8 -> 94.1 us with 256, 1048576x64 89.3 -> 91.6 us);
+    // otherwise at most 64
+    const int64_t txs = e == 8 ? (n <= 32 ? 256 : 128) : 256;
+    const int64_t tx = pow2_at_least(cdiv(m, V), n <= kColShortN ? txs : 64);
     const int64_t ty = 256 / tx;
     c.txw = (int)tx;
     c.sp = block_split(cdiv(m, tx * V), n, ty * kColTileU, 1, e, kWaveBlocks, kColMinUnits);

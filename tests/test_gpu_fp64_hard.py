@@ -73,6 +73,7 @@ GEMV_SHAPES = [  # (layout, m, n, pad, kernel it selects)
     (ROW, 3000, 200, 0, "short-200"),
     (ROW, 300, 5001, 0, "realigned"),
     (COL, 5000, 64, 0, "col-tall"),
+    (COL, 5001, 32, 0, "col-tall-32"),
     (COL, 64, 100000, 0, "col-wide"),
     (COL, 1000, 1000, 0, "col-square"),
 ]

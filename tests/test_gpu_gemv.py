@@ -90,7 +90,7 @@ def test_tiny_exhaustive(dt, layout):
 
 
 SHAPES = [(1000, 777), (777, 1000), (64, 100003), (100003, 64), (100001, 5), (5, 100001),
-          (33, 250001), (250001, 33), (1, 70000), (70000, 1), (4097, 129)]
+          (33, 250001), (250001, 33), (1, 70000), (70000, 1), (4097, 129), (20003, 32)]
 
 
 @pytest.mark.parametrize("dt", DTYPES, ids=DT_IDS)
