@@ -1013,15 +1013,17 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": len(ops) * args.steps,
+            "clocks": clocks.summary(wall0, wall1),
+            "precision": precision,
+            "batched": batched,
+            "serving": serving,
+            # the per-operation table last, so that a reader of the end of
+            # the output sees it whole
             "ops_timing": f"after the timed steps, each operation {OP_CALLS} times back to back between two "
                           f"CUDA events, {OP_REPS} such pairs; us = mean per call issued from the host, "
                           f"us_graph = the same calls replayed from one CUDA graph (no host launch between "
                           f"the kernels)",
-            "clocks": clocks.summary(wall0, wall1),
             "ops": ops_report,
-            "precision": precision,
-            "batched": batched,
-            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
