@@ -113,3 +113,44 @@ def test_link_bound():
     assert abs(up_only - 210.7) < 1e-9
     both = bench.link_bound(10e9, 5e9, 5e9, {"h2d_GB_s": 100.0, "d2h_GB_s": 100.0, "both_GB_s": 100.0})
     assert abs(both - 100.0) < 1e-9                                     # the shared rate decides
+
+
+def test_fit_fixed_cost_recovers_a_line():
+    """t = t0 + bytes / bw is recovered exactly from points on the line, and
+    least squares splits symmetric noise evenly; fewer than two distinct
+    sizes give no fit."""
+    t0, bw = 6e-6, 7.3e12
+    pts = [(k * 272_630_272, t0 + k * 272_630_272 / bw) for k in (1, 2, 4, 8)]
+    f0, fbw = bench.fit_fixed_cost(pts)
+    assert abs(f0 - t0) < 1e-12 and abs(fbw / bw - 1) < 1e-9
+    noisy = [(b, t + (1e-7 if i % 2 else -1e-7)) for i, (b, t) in enumerate(pts)]
+    g0, gbw = bench.fit_fixed_cost(noisy)
+    assert abs(g0 - t0) < 2e-7 and abs(gbw / bw - 1) < 1e-2
+    assert bench.fit_fixed_cost(pts[:1]) == (None, None)
+    assert bench.fit_fixed_cost([pts[0], pts[0]]) == (None, None)
+    assert bench.fit_fixed_cost([(1.0, 2.0), (2.0, 1.0)])[1] is None   # falling time: no rate
+
+
+def test_roofline_of_picks_the_binding_resource():
+    """GER moves 16 bytes per 2 flops, so even FP64 GER is bound by HBM; a
+    FP64 GEMV's 2 flops per 8 bytes would outrun the FP64 pipe's nominal
+    2 FMA/clk/SM, so its roofline is the ALU one (the kernels take most of
+    those products off that pipe, which is why they can beat it)."""
+    hbm = 6697.8
+    ger = ("ger_row_f64", "ger", "f64", "row", 16384, 16384)
+    by = bench.alg_bytes("ger", "f64", 16384, 16384)
+    r = bench.roofline_of(ger, by / (6000.0 * 1e9), hbm, "measured")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - 6000.0) < 0.1 and abs(r["frac"] - 6000.0 / hbm) < 1e-4
+    assert r["algorithmic_bytes"] == by
+    traffic = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))["kernels"]["ger_row_f64"]
+    want = traffic["dram_bytes_per_launch"] if traffic["sha"] == bench.source_sha(traffic["sources"]) else None
+    assert r["traffic"] == want
+    gemv = ("gemv_row_sq_f64", "gemv", "f64", "row", 16384, 16384)
+    flops = bench.alg_flops("gemv", 16384, 16384)
+    r = bench.roofline_of(gemv, flops / 1.0e12, hbm, "measured")
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    peak = bench.SMS * bench.DP_FMA_PER_CLK_SM * 2 * bench.SM_MAX_MHZ * 1e6 / 1e12
+    assert abs(r["peak"] - peak) < 1e-3 and abs(r["achieved"] - 1.0) < 1e-3
+    f32 = ("gemv_row_sq_f32", "gemv", "f32", "row", 16384, 16384)
+    assert bench.roofline_of(f32, 1e-4, hbm, "measured")["bound"] == "hbm"   # FP32 has no ALU leg
